@@ -1,0 +1,191 @@
+/*
+ * xcorr.h -- C ABI of the GB300 X-stage: cross-multiply and integrate for an
+ * FX radio correlator.
+ *
+ * What the library computes (Sec. 1 and Sec. 2.1 of the paper: the X-stage
+ * forms, for every frequency channel and time sample, the outer product of
+ * the spectra of all inputs and integrates the products over time; Sec. 2.2.3,
+ * Eq. 1: all N_i (N_i + 1) / 2 input pairs, autocorrelations included):
+ *
+ *     V[c][i][j] = sum_t x[t][c][i] * conj(x[t][c][j]),   0 <= j <= i < N_i
+ *
+ * with N_i = 2 * n_stations inputs, input i = 2 * station + pol (the paper's
+ * N_i is "twice the number of antennas", Sec. 2.2.3).  The integration is the
+ * exact SUM over the samples given since the last reset; the paper's GPU
+ * "averages" (Sec. 2.4, Sec. 4), and the caller divides by the sample count
+ * returned with each dump.
+ *
+ * Input layout (Sec. 2.3 and Fig. 3: per time sample, every channel of every
+ * input), sample order [time][channel][station][pol], one element per
+ * complex sample:
+ *   XCORR_IN_CI4   uint8: high nibble = real, low nibble = imaginary, each
+ *                  4-bit two's complement in [-8, 7] (Sec. 2.3: "four bits
+ *                  for each component"; the nibble order is this library's
+ *                  reading, the paper does not fix it).
+ *   XCORR_IN_CI8   int8 pair (re, im), the unpacked 8-bit form of Sec. 2.4.
+ *   XCORR_IN_CF32  float pair (re, im), spectra from a GPU F-stage (Sec. 1).
+ *
+ * Output layout: the packed lower triangle per channel, pair index
+ * p(i, j) = i (i + 1) / 2 + j for i >= j, (re, im) interleaved:
+ * [channel][pair][2].  Element type: int32 for CI4 / CI8, float for CF32;
+ * with XCORR_DUMP_ADD_WIDE the caller's buffer is int64 / double instead.
+ * V[c][j][i] = conj(V[c][i][j]) is not stored.
+ *
+ * Threading and ordering: a plan may be used by one host thread at a time.
+ * execute and dump are stream-ordered and return without waiting for the GPU
+ * unless stated; plan_create and destroy synchronise the device.
+ *
+ * Errors: every call returns an xcorr_status and never aborts the process;
+ * xcorr_last_error() gives a message for the calling thread's last failure.
+ * Kernel-side failures (a bounded wait that ran out) are recorded in a device
+ * status word; xcorr_sync reports them, and every later call on the plan
+ * returns XCORR_ERR_DEVICE until xcorr_destroy.
+ */
+#ifndef XCORR_H
+#define XCORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    XCORR_OK = 0,
+    XCORR_ERR_INVALID_ARG = 1,  /* a size, pointer, alignment or flag is invalid          */
+    XCORR_ERR_UNSUPPORTED = 2,  /* valid request this build or device cannot serve       */
+    XCORR_ERR_OOM = 3,          /* device allocation failed                              */
+    XCORR_ERR_OVERFLOW = 4,     /* the integration would exceed the exact int32 range   */
+    XCORR_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the detail)  */
+    XCORR_ERR_DEVICE = 6,       /* a kernel reported a failure (bounded wait timed out) */
+    XCORR_ERR_BUDGET = 7        /* the plan's device memory exceeds hbm_budget_bytes    */
+} xcorr_status;
+
+typedef enum { XCORR_IN_CI4 = 0, XCORR_IN_CI8 = 1, XCORR_IN_CF32 = 2 } xcorr_in_fmt;
+
+typedef enum {
+    XCORR_ENGINE_AUTO = 0,      /* tensor cores where the format has a tensor path       */
+    XCORR_ENGINE_TENSOR = 1,    /* tcgen05 tensor-core X kernel                          */
+    XCORR_ENGINE_CUDA_CORE = 2  /* plain CUDA-core (dp4a) X kernel, integer formats only */
+} xcorr_engine;
+
+typedef struct {
+    int n_stations;          /* >= 1; N_i = 2 * n_stations inputs                       */
+    int n_pols;              /* must be 2 (dual polarisation, Sec. 2.2.3)               */
+    int n_channels;          /* >= 1                                                    */
+    int max_time_per_exec;   /* >= 1; largest n_time one xcorr_execute may pass         */
+    xcorr_in_fmt fmt;
+    xcorr_engine engine;
+    size_t hbm_budget_bytes; /* 0 = no limit; else plan_create fails with BUDGET above it */
+} xcorr_config;
+
+typedef struct xcorr_plan_s *xcorr_plan;
+
+/* Opaque to the caller except through these fields (xcorr_plan_query). */
+typedef struct {
+    int n_inputs;             /* N_i = 2 * n_stations                                    */
+    int n_channels;
+    int64_t n_pairs;          /* N_i (N_i + 1) / 2                                       */
+    int engine;               /* the engine actually selected (never AUTO)               */
+    int64_t samples_integrated; /* samples accumulated since the last reset              */
+    int64_t max_integration;  /* most samples one integration may hold exactly in int32 */
+    size_t device_bytes;      /* device memory the plan owns                             */
+    size_t output_bytes;      /* bytes of one dump in the plan's own element type        */
+} xcorr_plan_info;
+
+/*
+ * Create a plan.  Validates cfg, allocates the device accumulator and any
+ * staging buffers on the current device (the plan owns them), and selects the
+ * kernels.  *out receives the plan, or NULL on failure.
+ * Errors: INVALID_ARG (bad sizes, n_pols != 2, NULL pointers), UNSUPPORTED
+ * (no GB300-class device, or CF32 with the CUDA-core engine), BUDGET, OOM, CUDA.
+ */
+xcorr_status xcorr_plan_create(xcorr_plan *out, const xcorr_config *cfg);
+
+/*
+ * Correlate n_time samples and add them to the running integration
+ * (Sec. 2.1: cross multiplication and integration per channel and sample).
+ * d_in: caller-owned DEVICE memory, [n_time][n_channels][n_stations][2]
+ * samples in the plan's format (any alignment; 16-byte alignment and N_i a
+ * multiple of 16 take the vectorised paths), read-only; it must stay
+ * valid until the stream passes this call.  1 <= n_time <= max_time_per_exec.
+ * stream: a cudaStream_t (NULL = the legacy default stream).
+ * Errors: INVALID_ARG, OVERFLOW (samples since reset + n_time would exceed
+ * max_integration; nothing is launched), DEVICE, CUDA.
+ */
+xcorr_status xcorr_execute(xcorr_plan plan, const void *d_in, int n_time, void *stream);
+
+/* Flags for xcorr_dump. */
+#define XCORR_DUMP_RESET 1u     /* start a new integration after this dump               */
+#define XCORR_DUMP_ADD_WIDE 2u  /* out is int64 (CI4/CI8) or double (CF32) device memory,
+                                   and the integration is ADDED to it (the cross-dump
+                                   accumulation of Sec. 2.4 / Sec. 4, kept exact)        */
+
+/*
+ * Write the current integration to out in the output layout above.
+ * out_on_device != 0: out is device memory (required with ADD_WIDE);
+ * otherwise out is host memory (pinned for a truly asynchronous copy).
+ * *n_samples (may be NULL) receives the samples in this integration, the
+ * divisor of the paper's average.  The copy is stream-ordered: read out only
+ * after synchronising the stream.  Errors: INVALID_ARG, DEVICE, CUDA.
+ */
+xcorr_status xcorr_dump(xcorr_plan plan, void *out, int out_on_device, unsigned flags,
+                        void *stream, int64_t *n_samples);
+
+/* Wait for the stream and report any kernel-side failure (DEVICE). */
+xcorr_status xcorr_sync(xcorr_plan plan, void *stream);
+
+/* Describe the plan.  Errors: INVALID_ARG. */
+xcorr_status xcorr_plan_query(xcorr_plan plan, xcorr_plan_info *info);
+
+/*
+ * Kernel timing for benchmarks (no counterpart in the paper).  With
+ * capacity > 0 every later xcorr_execute records three CUDA events on its
+ * stream: before the unpack kernel, between the unpack and the X kernel, and
+ * after the X kernel (the CUDA-core engine has no unpack, so its first
+ * interval is empty).  The last `capacity` executes are kept; capacity 0
+ * turns timing off.  Errors: INVALID_ARG, CUDA.
+ */
+xcorr_status xcorr_profile_enable(xcorr_plan plan, int capacity);
+
+/*
+ * Wait for the recorded events and write, oldest first, two durations in ms
+ * per timed execute: ms[2k] the unpack kernel, ms[2k + 1] the X kernel.
+ * `capacity` is the number of executes ms has room for; *count receives how
+ * many were written.  Errors: INVALID_ARG, CUDA.
+ */
+xcorr_status xcorr_profile_read(xcorr_plan plan, float *ms, int capacity, int *count);
+
+/*
+ * Measure a dense arithmetic rate of the current device in tera-operations
+ * per second (two operations per multiply-add), for stating fractions of
+ * peak; no counterpart in the paper.  kind 0: tcgen05 E4M3 MMA (the tensor
+ * X kernel's instruction), 1: tcgen05 BF16 MMA, 2: the int8 tensor path of
+ * sm_103a (warp-level mma.sync s8; tcgen05 has no int8 kind there), 3: CUDA-
+ * core dp4a.  Runs for tens of milliseconds and synchronises the device.
+ * Errors: INVALID_ARG, CUDA, DEVICE.
+ */
+xcorr_status xcorr_measure_peak(int kind, double *tops);
+
+/* Synchronise the device, free the plan's memory and the plan.  NULL is a no-op. */
+xcorr_status xcorr_destroy(xcorr_plan plan);
+
+/* Message for the calling thread's last failed call ("" if none).  Owned by the library. */
+const char *xcorr_last_error(void);
+
+/*
+ * Map a station pair and polarisation product to the packed triangle
+ * (recovers the "baselines x four polarisation products" view of Eq. 4 from
+ * the input-pair triangle).  V(a, p; b, q) = x_{a,p} conj(x_{b,q}) for
+ * stations a >= b, pols p, q in {0, 1}.  *idx receives p(i, j) of the stored
+ * pair and *conj is 1 when the requested product is the conjugate of the
+ * stored one (only for a == b, p < q).  Errors: INVALID_ARG.
+ */
+xcorr_status xcorr_baseline_index(int n_stations, int a, int b, int p, int q, int64_t *idx,
+                                  int *conj);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XCORR_H */

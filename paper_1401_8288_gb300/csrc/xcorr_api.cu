@@ -1,0 +1,333 @@
+// xcorr_api.cu -- the C ABI (xcorr.h): plan validation, device memory owned
+// by the plan, kernel selection and stream-ordered launches.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "xcorr_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+xcorr_status fail(xcorr_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+xcorr_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(XCORR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int64_t n_pairs_of(int n_inputs) { return (int64_t)n_inputs * (n_inputs + 1) / 2; }
+
+// Checks common to every call on a live plan.
+xcorr_status plan_ok(xcorr_plan plan) {
+  if (!plan) return fail(XCORR_ERR_INVALID_ARG, "plan is NULL");
+  if (!plan->sticky && plan->status_host && *const_cast<volatile int*>(plan->status_host) != 0)
+    plan->sticky = *plan->status_host;
+  if (plan->sticky)
+    return fail(XCORR_ERR_DEVICE, "a kernel of this plan reported failure code " + std::to_string(plan->sticky) +
+                                      " (a bounded wait ran out); destroy the plan");
+  cudaError_t e = cudaSetDevice(plan->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return XCORR_OK;
+}
+
+void free_profile(xcorr_plan plan) {
+  if (plan->prof_events) {
+    for (int k = 0; k < 3 * plan->prof_cap; ++k)
+      if (plan->prof_events[k]) cudaEventDestroy(plan->prof_events[k]);
+    delete[] plan->prof_events;
+  }
+  plan->prof_events = nullptr;
+  plan->prof_cap = 0;
+  plan->prof_count = 0;
+}
+
+void release(xcorr_plan plan) {
+  free_profile(plan);
+  if (plan->acc) cudaFree(plan->acc);
+  if (plan->planes) cudaFree(plan->planes);
+  if (plan->status) cudaFree(plan->status);
+  if (plan->status_host) cudaFreeHost(plan->status_host);
+  plan->acc = nullptr;
+  plan->planes = nullptr;
+  plan->status = nullptr;
+  plan->status_host = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* xcorr_last_error(void) { return g_last_error.c_str(); }
+
+xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
+  if (!out) return fail(XCORR_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(XCORR_ERR_INVALID_ARG, "cfg is NULL");
+  const xcorr_config c = *cfg;
+  if (c.n_pols != 2) return fail(XCORR_ERR_INVALID_ARG, "n_pols must be 2");
+  if (c.n_stations < 1 || c.n_stations > (1 << 20))
+    return fail(XCORR_ERR_INVALID_ARG, "n_stations must be in [1, 2^20]");
+  if (c.n_channels < 1) return fail(XCORR_ERR_INVALID_ARG, "n_channels must be >= 1");
+  if (c.max_time_per_exec < 1) return fail(XCORR_ERR_INVALID_ARG, "max_time_per_exec must be >= 1");
+  if (c.fmt != XCORR_IN_CI4 && c.fmt != XCORR_IN_CI8 && c.fmt != XCORR_IN_CF32)
+    return fail(XCORR_ERR_INVALID_ARG, "unknown input format");
+  if (c.engine != XCORR_ENGINE_AUTO && c.engine != XCORR_ENGINE_TENSOR && c.engine != XCORR_ENGINE_CUDA_CORE)
+    return fail(XCORR_ERR_INVALID_ARG, "unknown engine");
+
+  int engine = c.engine;
+  if (c.fmt == XCORR_IN_CF32)
+    return fail(XCORR_ERR_UNSUPPORTED, "the float input path is not available in this build");
+  if (engine == XCORR_ENGINE_AUTO) engine = (c.fmt == XCORR_IN_CI4) ? XCORR_ENGINE_TENSOR : XCORR_ENGINE_CUDA_CORE;
+  if (engine == XCORR_ENGINE_TENSOR && c.fmt != XCORR_IN_CI4)
+    return fail(XCORR_ERR_UNSUPPORTED, "the tensor-core engine takes 4-bit input in this build");
+
+  const int64_t max_int = (c.fmt == XCORR_IN_CI4) ? xc::kMaxIntegrationCI4 : xc::kMaxIntegrationCI8;
+  if (c.max_time_per_exec > max_int)
+    return fail(XCORR_ERR_OVERFLOW, "max_time_per_exec exceeds the exact int32 integration bound of " +
+                                        std::to_string(max_int) + " samples");
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(XCORR_ERR_UNSUPPORTED, std::string("this library is built for sm_103a (GB300); device is ") +
+                                           prop.name + " sm_" + std::to_string(prop.major * 10 + prop.minor));
+
+  const int n_inputs = 2 * c.n_stations;
+  const int ni_pad = (n_inputs + 15) / 16 * 16;
+  const int64_t n_pairs = n_pairs_of(n_inputs);
+  const size_t acc_bytes = (size_t)c.n_channels * (size_t)n_pairs * sizeof(int2);
+  const size_t planes_bytes =
+      engine == XCORR_ENGINE_TENSOR ? (size_t)c.n_channels * 2 * (size_t)c.max_time_per_exec * ni_pad : 0;
+  const size_t dev_bytes = acc_bytes + planes_bytes + 256;
+  if (c.hbm_budget_bytes && dev_bytes > c.hbm_budget_bytes)
+    return fail(XCORR_ERR_BUDGET, "plan needs " + std::to_string(dev_bytes) + " device bytes, budget is " +
+                                      std::to_string(c.hbm_budget_bytes));
+
+  xcorr_plan plan = new (std::nothrow) xcorr_plan_s();
+  if (!plan) return fail(XCORR_ERR_OOM, "host allocation failed");
+  plan->cfg = c;
+  plan->cfg.engine = static_cast<xcorr_engine>(engine);
+  plan->device = dev;
+  plan->num_sms = prop.multiProcessorCount;
+  plan->n_inputs = n_inputs;
+  plan->ni_pad = ni_pad;
+  plan->n_pairs = n_pairs;
+  plan->engine = engine;
+  plan->max_integration = max_int;
+  plan->planes_bytes = planes_bytes;
+  plan->device_bytes = dev_bytes;
+
+  if ((e = cudaMalloc(&plan->acc, acc_bytes)) != cudaSuccess ||
+      (planes_bytes && (e = cudaMalloc(&plan->planes, planes_bytes)) != cudaSuccess) ||
+      (e = cudaMalloc(&plan->status, 256)) != cudaSuccess ||
+      (e = cudaMallocHost(&plan->status_host, sizeof(int))) != cudaSuccess) {
+    release(plan);
+    delete plan;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? XCORR_ERR_OOM : XCORR_ERR_CUDA,
+                std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  *plan->status_host = 0;
+  if ((e = cudaMemset(plan->status, 0, 256)) != cudaSuccess ||
+      (e = cudaDeviceSynchronize()) != cudaSuccess) {
+    release(plan);
+    delete plan;
+    return cuda_fail(e, "plan initialisation");
+  }
+  *out = plan;
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_execute(xcorr_plan plan, const void* d_in, int n_time, void* stream) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  if (!d_in) return fail(XCORR_ERR_INVALID_ARG, "d_in is NULL");
+  if (n_time < 1 || n_time > plan->cfg.max_time_per_exec)
+    return fail(XCORR_ERR_INVALID_ARG, "n_time must be in [1, max_time_per_exec]");
+  if (plan->samples + n_time > plan->max_integration)
+    return fail(XCORR_ERR_OVERFLOW, "the integration would exceed " + std::to_string(plan->max_integration) +
+                                        " samples, the exact int32 bound; dump with reset first");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int C = plan->cfg.n_channels, N = plan->n_inputs;
+  cudaError_t e;
+  cudaEvent_t* ev = nullptr;
+  if (plan->prof_cap) {
+    ev = plan->prof_events + 3 * (plan->prof_count % plan->prof_cap);
+    if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return cuda_fail(e, "profile event");
+  }
+  if (plan->engine == XCORR_ENGINE_TENSOR) {
+    e = xc::launch_unpack_ci4_e4m3(static_cast<const uint8_t*>(d_in), plan->planes, n_time, C, N, plan->ni_pad,
+                                   plan->cfg.max_time_per_exec, plan->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "unpack launch");
+    if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "profile event");
+    if (plan->tmap_ntime != n_time) {
+      std::string err;
+      if (!xc::encode_plane_tmap(&plan->tmap, plan->planes, N, plan->ni_pad, n_time, plan->cfg.max_time_per_exec,
+                                 C, &err))
+        return fail(XCORR_ERR_CUDA, err);
+      plan->tmap_ntime = n_time;
+    }
+    e = xc::launch_xcorr_tc_e4m3(&plan->tmap, n_time, C, N, plan->acc, !plan->fresh, plan->status, plan->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core X kernel launch");
+  } else {
+    const int ks = xc::cuda_core_ksplit(n_time, C, N, plan->num_sms);
+    int mode = plan->fresh ? xc::MODE_STORE : xc::MODE_ADD;
+    if (ks > 1) {
+      if (plan->fresh) {
+        e = cudaMemsetAsync(plan->acc, 0, (size_t)C * plan->n_pairs * sizeof(int2), s);
+        if (e != cudaSuccess) return cuda_fail(e, "accumulator clear");
+      }
+      mode = xc::MODE_ATOMIC;
+    }
+    if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "profile event");
+    e = xc::launch_xcorr_cuda_core(plan->cfg.fmt, d_in, n_time, C, N, plan->acc, mode, ks, s);
+    if (e != cudaSuccess) return cuda_fail(e, "CUDA-core X kernel launch");
+  }
+  if (ev) {
+    if ((e = cudaEventRecord(ev[2], s)) != cudaSuccess) return cuda_fail(e, "profile event");
+    ++plan->prof_count;
+  }
+  plan->samples += n_time;
+  plan->fresh = false;
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_dump(xcorr_plan plan, void* out, int out_on_device, unsigned flags, void* stream,
+                        int64_t* n_samples) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  if (!out) return fail(XCORR_ERR_INVALID_ARG, "out is NULL");
+  if (flags & ~(XCORR_DUMP_RESET | XCORR_DUMP_ADD_WIDE)) return fail(XCORR_ERR_INVALID_ARG, "unknown dump flag");
+  const bool wide = (flags & XCORR_DUMP_ADD_WIDE) != 0;
+  if (wide && !out_on_device) return fail(XCORR_ERR_INVALID_ARG, "XCORR_DUMP_ADD_WIDE needs device memory");
+  if (wide && reinterpret_cast<uintptr_t>(out) % 16)
+    return fail(XCORR_ERR_INVALID_ARG, "the wide output must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t total = (int64_t)plan->cfg.n_channels * plan->n_pairs;
+  const size_t bytes = (size_t)total * sizeof(int2);
+  cudaError_t e;
+  if (plan->fresh) {  // nothing integrated since the last reset: the integration is zero
+    e = cudaMemsetAsync(plan->acc, 0, bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "accumulator clear");
+    plan->fresh = false;
+  }
+  if (wide) {
+    e = xc::launch_fold_wide_i64(plan->acc, static_cast<int64_t*>(out), total, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fold launch");
+  } else {
+    e = cudaMemcpyAsync(out, plan->acc, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "dump copy");
+  }
+  e = cudaMemcpyAsync(plan->status_host, plan->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  if (n_samples) *n_samples = plan->samples;
+  if (flags & XCORR_DUMP_RESET) {
+    plan->samples = 0;
+    plan->fresh = true;
+  }
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_sync(xcorr_plan plan, void* stream) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int code = 0;
+  e = cudaMemcpy(&code, plan->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (code) {
+    plan->sticky = code;
+    return plan_ok(plan);
+  }
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_plan_query(xcorr_plan plan, xcorr_plan_info* info) {
+  if (!plan || !info) return fail(XCORR_ERR_INVALID_ARG, "plan or info is NULL");
+  info->n_inputs = plan->n_inputs;
+  info->n_channels = plan->cfg.n_channels;
+  info->n_pairs = plan->n_pairs;
+  info->engine = plan->engine;
+  info->samples_integrated = plan->samples;
+  info->max_integration = plan->max_integration;
+  info->device_bytes = plan->device_bytes;
+  info->output_bytes = (size_t)plan->cfg.n_channels * plan->n_pairs * sizeof(int2);
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_profile_enable(xcorr_plan plan, int capacity) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  if (capacity < 0 || capacity > (1 << 20)) return fail(XCORR_ERR_INVALID_ARG, "capacity must be in [0, 2^20]");
+  free_profile(plan);
+  if (capacity == 0) return XCORR_OK;
+  plan->prof_events = new (std::nothrow) cudaEvent_t[3 * (size_t)capacity]();
+  if (!plan->prof_events) return fail(XCORR_ERR_OOM, "host allocation failed");
+  plan->prof_cap = capacity;
+  for (int k = 0; k < 3 * capacity; ++k) {
+    cudaError_t e = cudaEventCreate(&plan->prof_events[k]);
+    if (e != cudaSuccess) {
+      free_profile(plan);
+      return cuda_fail(e, "cudaEventCreate");
+    }
+  }
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_profile_read(xcorr_plan plan, float* ms, int capacity, int* count) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  if (!ms || !count || capacity < 0) return fail(XCORR_ERR_INVALID_ARG, "ms or count is NULL");
+  *count = 0;
+  if (!plan->prof_cap) return XCORR_OK;
+  const int64_t have = plan->prof_count < plan->prof_cap ? plan->prof_count : plan->prof_cap;
+  const int64_t n = have < capacity ? have : capacity;
+  for (int64_t k = 0; k < n; ++k) {
+    const int64_t launch = plan->prof_count - n + k;
+    cudaEvent_t* ev = plan->prof_events + 3 * (launch % plan->prof_cap);
+    cudaError_t e = cudaEventSynchronize(ev[2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[2 * k], ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[2 * k + 1], ev[1], ev[2]);
+    if (e != cudaSuccess) return cuda_fail(e, "profile read");
+  }
+  *count = static_cast<int>(n);
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_destroy(xcorr_plan plan) {
+  if (!plan) return XCORR_OK;
+  cudaSetDevice(plan->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  release(plan);
+  delete plan;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize at destroy");
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_baseline_index(int n_stations, int a, int b, int p, int q, int64_t* idx, int* conj) {
+  if (!idx || !conj) return fail(XCORR_ERR_INVALID_ARG, "idx or conj is NULL");
+  if (n_stations < 1 || a < 0 || a >= n_stations || b < 0 || b > a || p < 0 || p > 1 || q < 0 || q > 1)
+    return fail(XCORR_ERR_INVALID_ARG, "need 0 <= b <= a < n_stations and pols in {0, 1}");
+  int64_t i = 2LL * a + p, j = 2LL * b + q;
+  *conj = 0;
+  if (j > i) {  // only for a == b, p < q: the stored pair is (j, i)
+    const int64_t t = i;
+    i = j;
+    j = t;
+    *conj = 1;
+  }
+  *idx = i * (i + 1) / 2 + j;
+  return XCORR_OK;
+}
+
+}  // extern "C"

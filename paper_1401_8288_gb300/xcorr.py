@@ -1,0 +1,230 @@
+"""Thin Python binding of the C ABI in ``include/xcorr.h``.
+
+The functions below carry the C names and only marshal arguments: every step
+of the X-stage runs in the library's CUDA kernels.  Device buffers are plain
+pointers (``tensor.data_ptr()``) and streams are ``cudaStream_t`` handles
+(``torch.cuda.current_stream().cuda_stream``); ``Plan`` wraps both with
+PyTorch tensors for convenience.  If the library has not been built this
+module raises on first use -- there is no fallback path.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+XCORR_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "OVERFLOW",
+                5: "CUDA", 6: "DEVICE", 7: "BUDGET"}
+XCORR_IN_CI4, XCORR_IN_CI8, XCORR_IN_CF32 = 0, 1, 2
+XCORR_ENGINE_AUTO, XCORR_ENGINE_TENSOR, XCORR_ENGINE_CUDA_CORE = 0, 1, 2
+XCORR_DUMP_RESET, XCORR_DUMP_ADD_WIDE = 1, 2
+
+FORMATS = {"ci4": XCORR_IN_CI4, "ci8": XCORR_IN_CI8, "cf32": XCORR_IN_CF32}
+ENGINES = {"auto": XCORR_ENGINE_AUTO, "tensor": XCORR_ENGINE_TENSOR,
+           "cuda_core": XCORR_ENGINE_CUDA_CORE}
+
+EXPORTS = ("xcorr_plan_create", "xcorr_execute", "xcorr_dump", "xcorr_sync", "xcorr_plan_query",
+           "xcorr_destroy", "xcorr_last_error", "xcorr_baseline_index", "xcorr_profile_enable",
+           "xcorr_profile_read", "xcorr_measure_peak")
+PEAK_KINDS = {"tc_e4m3": 0, "tc_bf16": 1, "mma_sync_s8": 2, "dp4a": 3}
+
+
+class XcorrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"xcorr {STATUS_NAMES.get(status, status)}: {message}")
+
+
+class xcorr_config(ctypes.Structure):
+    _fields_ = [("n_stations", ctypes.c_int), ("n_pols", ctypes.c_int),
+                ("n_channels", ctypes.c_int), ("max_time_per_exec", ctypes.c_int),
+                ("fmt", ctypes.c_int), ("engine", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+class xcorr_plan_info(ctypes.Structure):
+    _fields_ = [("n_inputs", ctypes.c_int), ("n_channels", ctypes.c_int),
+                ("n_pairs", ctypes.c_int64), ("engine", ctypes.c_int),
+                ("samples_integrated", ctypes.c_int64), ("max_integration", ctypes.c_int64),
+                ("device_bytes", ctypes.c_size_t), ("output_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load ``libxcorr.so`` (build it first with ``paper_1401_8288_gb300.build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"{_build.LIB} is missing: build the CUDA library first "
+                                   "(python -m paper_1401_8288_gb300.build)")
+            lib = ctypes.CDLL(_build.LIB)
+            vp, i, u, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_int64
+            sig = {
+                "xcorr_plan_create": [ctypes.POINTER(vp), ctypes.POINTER(xcorr_config)],
+                "xcorr_execute": [vp, vp, i, vp],
+                "xcorr_dump": [vp, vp, i, u, vp, ctypes.POINTER(i64)],
+                "xcorr_sync": [vp, vp],
+                "xcorr_plan_query": [vp, ctypes.POINTER(xcorr_plan_info)],
+                "xcorr_destroy": [vp],
+                "xcorr_baseline_index": [i, i, i, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)],
+                "xcorr_profile_enable": [vp, i],
+                "xcorr_profile_read": [vp, ctypes.POINTER(ctypes.c_float), i, ctypes.POINTER(i)],
+                "xcorr_measure_peak": [i, ctypes.POINTER(ctypes.c_double)],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            lib.xcorr_last_error.argtypes = []
+            lib.xcorr_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def xcorr_last_error() -> str:
+    return load().xcorr_last_error().decode()
+
+
+def _check(status: int) -> None:
+    if status != XCORR_OK:
+        raise XcorrError(status, xcorr_last_error())
+
+
+def xcorr_plan_create(n_stations: int, n_channels: int, max_time_per_exec: int,
+                      fmt: int = XCORR_IN_CI4, engine: int = XCORR_ENGINE_AUTO,
+                      hbm_budget_bytes: int = 0, n_pols: int = 2) -> ctypes.c_void_p:
+    cfg = xcorr_config(n_stations, n_pols, n_channels, max_time_per_exec, fmt, engine,
+                       hbm_budget_bytes)
+    plan = ctypes.c_void_p()
+    _check(load().xcorr_plan_create(ctypes.byref(plan), ctypes.byref(cfg)))
+    return plan
+
+
+def xcorr_execute(plan, d_in: int, n_time: int, stream: int = 0) -> None:
+    _check(load().xcorr_execute(plan, d_in, n_time, stream))
+
+
+def xcorr_dump(plan, out: int, out_on_device: bool, flags: int = 0, stream: int = 0) -> int:
+    n = ctypes.c_int64()
+    _check(load().xcorr_dump(plan, out, int(out_on_device), flags, stream, ctypes.byref(n)))
+    return n.value
+
+
+def xcorr_sync(plan, stream: int = 0) -> None:
+    _check(load().xcorr_sync(plan, stream))
+
+
+def xcorr_plan_query(plan) -> dict:
+    info = xcorr_plan_info()
+    _check(load().xcorr_plan_query(plan, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in xcorr_plan_info._fields_}
+
+
+def xcorr_destroy(plan) -> None:
+    _check(load().xcorr_destroy(plan))
+
+
+def xcorr_baseline_index(n_stations: int, a: int, b: int, p: int, q: int) -> tuple[int, bool]:
+    idx, conj = ctypes.c_int64(), ctypes.c_int()
+    _check(load().xcorr_baseline_index(n_stations, a, b, p, q, ctypes.byref(idx),
+                                       ctypes.byref(conj)))
+    return idx.value, bool(conj.value)
+
+
+def xcorr_profile_enable(plan, capacity: int) -> None:
+    _check(load().xcorr_profile_enable(plan, capacity))
+
+
+def xcorr_profile_read(plan, capacity: int) -> list[tuple[float, float]]:
+    """(unpack ms, X-kernel ms) of the last timed executes, oldest first."""
+    buf = (ctypes.c_float * (2 * max(capacity, 1)))()
+    n = ctypes.c_int()
+    _check(load().xcorr_profile_read(plan, buf, capacity, ctypes.byref(n)))
+    return [(buf[2 * k], buf[2 * k + 1]) for k in range(n.value)]
+
+
+def xcorr_measure_peak(kind: str | int) -> float:
+    """Measured dense rate (TOPS) of one arithmetic path of the current device."""
+    k = PEAK_KINDS.get(kind, kind)
+    tops = ctypes.c_double()
+    st = load().xcorr_measure_peak(k, ctypes.byref(tops))
+    if st != XCORR_OK:
+        raise XcorrError(st, f"peak measurement of kind {kind} failed")
+    return tops.value
+
+
+class Plan:
+    """A plan with PyTorch tensors for device memory and streams.
+
+    ``execute(x)`` takes a CUDA tensor in the plan's input layout
+    (uint8 [t][c][s][2] for CI4, int8 [t][c][s][2][2] for CI8);
+    ``dump()`` returns the packed-triangle visibilities as an int32 tensor
+    [C][P][2] (or writes them into ``out``).
+    """
+
+    def __init__(self, n_stations: int, n_channels: int, max_time_per_exec: int,
+                 fmt: str = "ci4", engine: str = "auto", hbm_budget_bytes: int = 0):
+        import torch  # device memory and streams only
+        self._torch = torch
+        self.fmt = fmt
+        self.handle = xcorr_plan_create(n_stations, n_channels, max_time_per_exec,
+                                        FORMATS[fmt], ENGINES[engine], hbm_budget_bytes)
+        self.info = xcorr_plan_query(self.handle)
+        self.n_stations = n_stations
+        self.n_channels = n_channels
+
+    def _stream(self, stream) -> int:
+        if stream is None:
+            return self._torch.cuda.current_stream().cuda_stream
+        return getattr(stream, "cuda_stream", stream)
+
+    def execute(self, x, n_time: int | None = None, stream=None) -> None:
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("input must be a contiguous CUDA tensor")
+        xcorr_execute(self.handle, x.data_ptr(), x.shape[0] if n_time is None else n_time,
+                      self._stream(stream))
+
+    def dump(self, out=None, reset: bool = True, wide: bool = False, stream=None):
+        torch = self._torch
+        shape = (self.n_channels, self.info["n_pairs"], 2)
+        if out is None:
+            out = torch.zeros(shape, dtype=torch.int64 if wide else torch.int32, device="cuda")
+        flags = (XCORR_DUMP_RESET if reset else 0) | (XCORR_DUMP_ADD_WIDE if wide else 0)
+        self.samples = xcorr_dump(self.handle, out.data_ptr(), out.is_cuda, flags,
+                                  self._stream(stream))
+        return out
+
+    def sync(self, stream=None) -> None:
+        xcorr_sync(self.handle, self._stream(stream))
+
+    def query(self) -> dict:
+        return xcorr_plan_query(self.handle)
+
+    def close(self) -> None:
+        if self.handle is not None:
+            xcorr_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA library (through the C ABI) against the oracle.
+
+Integer inputs must match bit for bit.  Sizes span several 128 x 128 tensor
+tiles (and 64 x 64 CUDA-core tiles) with ragged input and time tails; the
+full-size workloads are checked on sampled channels and sampled pairs, which
+the oracle computes one by one.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_8288_gb300 import synth, xcorr
+
+pytestmark = pytest.mark.gpu
+
+ENGINES = ["tensor", "cuda_core"]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1401_8288_gb300 import build
+    build.build()
+    return torch
+
+
+def run(torch, x, engine, fmt="ci4", n_time=None, chunks=None):
+    """Correlate x (host array) with one plan; optionally in several executes."""
+    n_time = x.shape[0] if n_time is None else n_time
+    n_sta, n_chan = x.shape[2], x.shape[1]
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    max_t = n_time if chunks is None else max(chunks)
+    with xcorr.Plan(n_sta, n_chan, max_t, fmt=fmt, engine=engine) as plan:
+        if chunks is None:
+            plan.execute(xd)
+        else:
+            t0 = 0
+            for k in chunks:
+                plan.execute(xd[t0:t0 + k])
+                t0 += k
+        out = plan.dump()
+        plan.sync()
+        return out.cpu().numpy().astype(np.int64), plan.samples
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("n_sta,n_chan,n_time", [
+    (1, 1, 1), (1, 2, 5), (3, 2, 33), (8, 1, 128), (32, 3, 129), (64, 2, 256),
+    (70, 3, 300), (100, 2, 200), (136, 2, 131), (200, 1, 385)])
+def test_small_shapes_bit_exact(torch, engine, n_sta, n_chan, n_time):
+    x = synth.uniform_ci4(n_time, n_chan, n_sta, seed=n_sta * 1000 + n_time, lo=-8, hi=7)
+    got, n = run(torch, x, engine)
+    assert n == n_time
+    want = oracle.correlate(oracle.FMT_CI4, x)
+    assert got.shape == want.shape
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_odd_input_count_not_multiple_of_16(torch, engine):
+    # 2 * 9 = 18 inputs: the unpack and the loaders take their unaligned paths
+    x = synth.uniform_ci4(77, 3, 9, seed=5, lo=-8, hi=7)
+    got, _ = run(torch, x, engine)
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_extreme_codes(torch, engine):
+    # every sample -8 - 8j: the largest per-sample products
+    k = 1000
+    x = np.full((k, 2, 70, 2), 0x88, dtype=np.uint8)
+    got, _ = run(torch, x, engine)
+    assert np.all(got[..., 0] == 128 * k) and np.all(got[..., 1] == 0)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_quarter_turn_tone(torch, engine):
+    x, q = synth.quarter_turn_tone_ci4(257, 2, 66, seed=9, amp=7)
+    got, _ = run(torch, x, engine)
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_integration_over_several_executes(torch, engine):
+    chunks = [200, 77, 256, 1]
+    x = synth.uniform_ci4(sum(chunks), 2, 70, seed=13, lo=-8, hi=7)
+    got, n = run(torch, x, engine, chunks=chunks)
+    assert n == sum(chunks)
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+def test_tensor_window_drain_beyond_2_24_partial_sums(torch):
+    # 140,000 samples, mostly -8 - 8j (|x|^2 = 128) with 7 - 2j (|x|^2 = 53,
+    # odd) every 101st sample: the autocorrelations pass 2^24, where FP32
+    # cannot hold odd increments, so the kernel must drain windows into int32.
+    k = 140000
+    x = np.full((k, 1, 8, 2), 0x88, dtype=np.uint8)
+    x[::101] = 0x7E
+    want = oracle.correlate(oracle.FMT_CI4, x)
+    assert want[0, 0, 0] > 2**24
+    got, _ = run(torch, x, "tensor")
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_dump_reset_and_wide_fold(torch, engine):
+    x = synth.uniform_ci4(96, 2, 40, seed=21, lo=-8, hi=7)
+    want = oracle.correlate(oracle.FMT_CI4, x)
+    xd = torch.from_numpy(x).cuda()
+    with xcorr.Plan(40, 2, 96, engine=engine) as plan:
+        wide = torch.zeros((2, plan.info["n_pairs"], 2), dtype=torch.int64, device="cuda")
+        plan.execute(xd)
+        a = plan.dump(reset=False)                      # keep integrating
+        plan.dump(out=wide, wide=True, reset=True)      # fold into int64, restart
+        plan.execute(xd)
+        plan.execute(xd)
+        plan.dump(out=wide, wide=True, reset=True)      # + two more passes
+        empty = plan.dump()                             # nothing since the reset
+        plan.sync()
+        assert np.array_equal(a.cpu().numpy(), want)
+        assert np.array_equal(wide.cpu().numpy(), 3 * want)
+        assert np.all(empty.cpu().numpy() == 0)
+        host = np.zeros_like(want, dtype=np.int32)
+        plan.execute(xd)
+        n = xcorr.xcorr_dump(plan.handle, host.ctypes.data, False, xcorr.XCORR_DUMP_RESET, 0)
+        plan.sync(0)
+        torch.cuda.synchronize()
+        assert n == 96 and np.array_equal(host, want)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("fmt", ["ci4", "ci8"])
+def test_input_at_any_byte_offset(torch, engine, fmt):
+    # a time slice of a larger buffer starts at an arbitrary byte: the kernels
+    # take their unaligned paths and stay exact
+    if fmt == "ci8" and engine == "tensor":
+        pytest.skip("the tensor engine takes 4-bit input")
+    n_time, n_chan, n_sta = 50, 2, 32
+    if fmt == "ci4":
+        x = synth.uniform_ci4(n_time, n_chan, n_sta, seed=31, lo=-8, hi=7)
+    else:
+        x = synth.uniform_ci8(n_time, n_chan, n_sta, seed=31)
+    raw = x.view(np.uint8).reshape(-1)
+    for off in (1, 2, 4, 8):
+        buf = torch.zeros(raw.size + 64, dtype=torch.uint8, device="cuda")
+        buf[off:off + raw.size] = torch.from_numpy(raw).cuda()
+        with xcorr.Plan(n_sta, n_chan, n_time, fmt=fmt, engine=engine) as plan:
+            xcorr.xcorr_execute(plan.handle, buf.data_ptr() + off, n_time, 0)
+            got = plan.dump(stream=0).cpu().numpy().astype(np.int64)
+            plan.sync(0)
+        want = oracle.correlate(oracle.FMT_CI4 if fmt == "ci4" else oracle.FMT_CI8, x)
+        assert np.array_equal(got, want), off
+
+
+def test_ci8_cuda_core_full_code_range(torch):
+    x = synth.uniform_ci8(150, 3, 37, seed=23)  # includes -128
+    got, _ = run(torch, x, "cuda_core", fmt="ci8")
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI8, x))
+
+
+def test_ci8_extreme_codes_at_the_int32_bound(torch):
+    # 65,535 samples of -128 - 128j: Re = 32768 * K = 2^31 - 32768, the largest exact sum
+    k = 65535
+    x = np.full((k, 1, 1, 2, 2), -128, dtype=np.int8)
+    got, _ = run(torch, x, "cuda_core", fmt="ci8")
+    assert np.all(got[..., 0] == 32768 * k) and np.all(got[..., 1] == 0)
+
+
+def test_errors_are_reported_not_raised_on_device(torch):
+    x = torch.zeros((16, 1, 4, 2), dtype=torch.uint8, device="cuda")
+    with xcorr.Plan(4, 1, 16, fmt="ci4") as plan:
+        with pytest.raises(xcorr.XcorrError) as e:
+            xcorr.xcorr_execute(plan.handle, x.data_ptr(), 17, 0)  # n_time > max
+        assert e.value.status == 1
+        with pytest.raises(xcorr.XcorrError):
+            xcorr.xcorr_dump(plan.handle, 0, True, 0, 0)
+        with pytest.raises(xcorr.XcorrError):
+            xcorr.xcorr_dump(plan.handle, x.data_ptr(), False, xcorr.XCORR_DUMP_ADD_WIDE, 0)
+    with xcorr.Plan(1, 1, 40000, fmt="ci8", engine="cuda_core") as plan:
+        y = torch.zeros((40000, 1, 1, 2, 2), dtype=torch.int8, device="cuda")
+        plan.execute(y)
+        with pytest.raises(xcorr.XcorrError) as e:
+            plan.execute(y)  # 80,000 samples would pass the exact int32 bound
+        assert e.value.status == 4
+        plan.dump(reset=True)
+        plan.execute(y)  # fine after the reset
+        plan.sync()
+
+
+def test_budget_and_query(torch):
+    with pytest.raises(xcorr.XcorrError) as e:
+        xcorr.Plan(256, 64, 2048, hbm_budget_bytes=1 << 20)
+    assert e.value.status == 7
+    with xcorr.Plan(256, 64, 2048) as plan:
+        info = plan.query()
+        assert info["n_inputs"] == 512 and info["n_pairs"] == 131328
+        assert info["engine"] == xcorr.XCORR_ENGINE_TENSOR
+        assert info["max_integration"] == 16777215
+        assert info["output_bytes"] == 64 * 131328 * 8
+
+
+# ------------------------------------------------- full-size workloads ---
+
+def sample_check(got, x, fmt, channels, n_pairs_sample, seed):
+    """Whole triangles of a few channels, then single pairs across all channels."""
+    for c in channels:
+        want = oracle.correlate(fmt, x, c0=c, c1=c + 1)[0]
+        assert np.array_equal(got[c], want), f"channel {c}"
+    rng = np.random.default_rng(seed)
+    n_chan, ni = got.shape[0], int((np.sqrt(8 * got.shape[1] + 1) - 1) / 2)
+    i = rng.integers(0, ni, size=n_pairs_sample)
+    j = (rng.random(n_pairs_sample) * (i + 1)).astype(np.int64)
+    c = rng.integers(0, n_chan, size=n_pairs_sample)
+    trips = np.stack([c, i, j], axis=1)
+    want = oracle.correlate_pairs(fmt, x, trips)
+    assert np.array_equal(got[c, i * (i + 1) // 2 + j], want)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_workload_64_inputs_64_channels_1024_samples(torch, engine):
+    # 32 stations x 2 pols, 64 channels, K = 1024, uniform [-7, 7]: checked whole
+    x = synth.uniform_ci4(1024, 64, 32, seed=14018288 + 1)
+    got, _ = run(torch, x, engine)
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+@pytest.fixture(scope="module")
+def workload_512():
+    # 256 stations x 2 pols, 512 channels, K = 2048, Gaussian sigma 2.5 + plane wave
+    return synth.gaussian_planewave_ci4(2048, 512, 256, seed=14018288 + 2)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_workload_512_inputs_512_channels_2048_samples(torch, workload_512, engine):
+    got, _ = run(torch, workload_512, engine)
+    sample_check(got, workload_512, oracle.FMT_CI4, channels=[0, 137, 511], n_pairs_sample=400,
+                 seed=3)
