@@ -168,6 +168,34 @@ xcorr_status xcorr_profile_read(xcorr_plan plan, float *ms, int capacity, int *c
  */
 xcorr_status xcorr_measure_peak(int kind, double *tops);
 
+/*
+ * One-shot 4-bit correlation that allocates no memory (the paper has no
+ * counterpart; this serves callers that cannot allocate when they correlate,
+ * such as a real-time capture loop in which cudaMalloc would synchronise the
+ * device and stall the streams draining the network, or code whose device
+ * memory belongs to another framework's fixed pool).
+ *
+ * Computes the same packed-triangle visibilities as a tensor-engine plan:
+ * d_in is CI4 device memory [n_time][n_channels][n_stations][2] (any
+ * alignment), d_out receives int32 [n_channels][P][2] (device memory, written,
+ * not added to).  d_status, if not NULL, is a device int that receives the
+ * kernels' status word (0 = success).  Both buffers are the caller's.
+ *
+ * The staging planes live in a fixed 64 MiB array that every GPU loading the
+ * library holds until the process exits; a call needs
+ * 2 * n_channels * n_time * round_up(2 * n_stations, 16) bytes of it and is
+ * refused with INVALID_ARG beyond 64 MiB - 256 bytes.  The first call on a
+ * device looks up the array's device address (make that first call before
+ * any stream capture).  Every call uses the same array and leaves its
+ * contents behind, so calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and must be serialised by the
+ * caller.  The call returns without waiting for the GPU.
+ * Errors: INVALID_ARG, OVERFLOW, UNSUPPORTED, CUDA.
+ */
+xcorr_status xcorr_correlate_ci4_noalloc(const void *d_in, int n_time, int n_channels,
+                                         int n_stations, void *d_out, int *d_status,
+                                         void *stream);
+
 /* Synchronise the device, free the plan's memory and the plan.  NULL is a no-op. */
 xcorr_status xcorr_destroy(xcorr_plan plan);
 

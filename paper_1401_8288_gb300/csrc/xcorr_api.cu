@@ -60,6 +60,10 @@ void release(xcorr_plan plan) {
 
 }  // namespace
 
+namespace xc {
+xcorr_status set_error(xcorr_status st, const std::string& msg) { return fail(st, msg); }
+}  // namespace xc
+
 extern "C" {
 
 const char* xcorr_last_error(void) { return g_last_error.c_str(); }

@@ -72,6 +72,9 @@ cudaError_t launch_xcorr_cuda_core(int fmt, const void* in, int n_time, int n_ch
 // Choose the CUDA-core kernel's split of the time axis (1 = no split).
 int cuda_core_ksplit(int n_time, int n_chan, int n_inputs, int num_sms);
 
+// Record the calling thread's error message (read by xcorr_last_error) and return st.
+xcorr_status set_error(xcorr_status st, const std::string& msg);
+
 cudaError_t launch_fold_wide_i64(const int2* acc, int64_t* out, int64_t n_pairs_total,
                                  cudaStream_t stream);
 

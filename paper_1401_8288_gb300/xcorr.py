@@ -29,7 +29,7 @@ ENGINES = {"auto": XCORR_ENGINE_AUTO, "tensor": XCORR_ENGINE_TENSOR,
 
 EXPORTS = ("xcorr_plan_create", "xcorr_execute", "xcorr_dump", "xcorr_sync", "xcorr_plan_query",
            "xcorr_destroy", "xcorr_last_error", "xcorr_baseline_index", "xcorr_profile_enable",
-           "xcorr_profile_read", "xcorr_measure_peak")
+           "xcorr_profile_read", "xcorr_measure_peak", "xcorr_correlate_ci4_noalloc")
 PEAK_KINDS = {"tc_e4m3": 0, "tc_bf16": 1, "mma_sync_s8": 2, "dp4a": 3}
 
 
@@ -82,6 +82,7 @@ def load():
                 "xcorr_profile_enable": [vp, i],
                 "xcorr_profile_read": [vp, ctypes.POINTER(ctypes.c_float), i, ctypes.POINTER(i)],
                 "xcorr_measure_peak": [i, ctypes.POINTER(ctypes.c_double)],
+                "xcorr_correlate_ci4_noalloc": [vp, i, i, i, vp, vp, vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -163,6 +164,15 @@ def xcorr_measure_peak(kind: str | int) -> float:
     if st != XCORR_OK:
         raise XcorrError(st, f"peak measurement of kind {kind} failed")
     return tops.value
+
+
+def xcorr_correlate_ci4_noalloc(d_in: int, n_time: int, n_channels: int, n_stations: int,
+                                d_out: int, d_status: int = 0, stream: int = 0) -> None:
+    """One-shot 4-bit correlation into caller memory, with no device allocation:
+    for callers that must not call the allocator (see include/xcorr.h).  Calls
+    share one fixed scratch array per GPU, so overlapping calls race."""
+    _check(load().xcorr_correlate_ci4_noalloc(d_in, n_time, n_channels, n_stations, d_out,
+                                              d_status or None, stream))
 
 
 class Plan:
