@@ -92,6 +92,7 @@ typedef struct {
     int64_t max_integration;  /* most samples one integration may hold exactly in int32 */
     size_t device_bytes;      /* device memory the plan owns                             */
     size_t output_bytes;      /* bytes of one dump in the plan's own element type        */
+    int kernels_per_execute;  /* kernel launches of one full-size execute (unpack + X)   */
 } xcorr_plan_info;
 
 /*
@@ -133,6 +134,19 @@ xcorr_status xcorr_execute(xcorr_plan plan, const void *d_in, int n_time, void *
 xcorr_status xcorr_dump(xcorr_plan plan, void *out, int out_on_device, unsigned flags,
                         void *stream, int64_t *n_samples);
 
+/*
+ * xcorr_execute followed by xcorr_dump with the same flags, in one call.
+ * When this execute is the whole integration (the plan was reset, flags
+ * hold XCORR_DUMP_RESET and not ADD_WIDE, and out is device memory) the X
+ * kernel writes the visibilities straight into out and the plan's own
+ * accumulator is not touched; otherwise it is exactly the two calls.
+ * Sec. 2.1 / Sec. 2.4: the GPU integrates and hands the matrix back.
+ * Errors: those of xcorr_execute and xcorr_dump.
+ */
+xcorr_status xcorr_execute_dump(xcorr_plan plan, const void *d_in, int n_time, void *out,
+                                int out_on_device, unsigned flags, void *stream,
+                                int64_t *n_samples);
+
 /* Wait for the stream and report any kernel-side failure (DEVICE). */
 xcorr_status xcorr_sync(xcorr_plan plan, void *stream);
 
@@ -141,17 +155,19 @@ xcorr_status xcorr_plan_query(xcorr_plan plan, xcorr_plan_info *info);
 
 /*
  * Kernel timing for benchmarks (no counterpart in the paper).  With
- * capacity > 0 every later xcorr_execute records three CUDA events on its
- * stream: before the unpack kernel, between the unpack and the X kernel, and
- * after the X kernel (the CUDA-core engine has no unpack, so its first
- * interval is empty).  The last `capacity` executes are kept; capacity 0
- * turns timing off.  Errors: INVALID_ARG, CUDA.
+ * capacity > 0 every later execute records CUDA events on the streams its
+ * kernels run on: at its start, after its last unpack kernel, and before and
+ * after every launch of the X kernel (the tensor path may split the channels
+ * into groups, each with its own launch; the CUDA-core engine has no unpack).
+ * The last `capacity` executes are kept; capacity 0 turns timing off.
+ * Errors: INVALID_ARG, CUDA.
  */
 xcorr_status xcorr_profile_enable(xcorr_plan plan, int capacity);
 
 /*
  * Wait for the recorded events and write, oldest first, two durations in ms
- * per timed execute: ms[2k] the unpack kernel, ms[2k + 1] the X kernel.
+ * per timed execute: ms[2k] from the start of the execute to the end of its
+ * last unpack kernel, ms[2k + 1] the summed durations of its X-kernel launches.
  * `capacity` is the number of executes ms has room for; *count receives how
  * many were written.  Errors: INVALID_ARG, CUDA.
  */

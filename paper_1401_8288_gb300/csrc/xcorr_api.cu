@@ -37,17 +37,29 @@ xcorr_status plan_ok(xcorr_plan plan) {
 
 void free_profile(xcorr_plan plan) {
   if (plan->prof_events) {
-    for (int k = 0; k < 3 * plan->prof_cap; ++k)
+    for (int64_t k = 0; k < (int64_t)xc::kProfileEvents * plan->prof_cap; ++k)
       if (plan->prof_events[k]) cudaEventDestroy(plan->prof_events[k]);
     delete[] plan->prof_events;
   }
+  delete[] plan->prof_ngroups;
   plan->prof_events = nullptr;
+  plan->prof_ngroups = nullptr;
   plan->prof_cap = 0;
   plan->prof_count = 0;
 }
 
 void release(xcorr_plan plan) {
   free_profile(plan);
+  if (plan->s_unpack) cudaStreamDestroy(plan->s_unpack);
+  for (auto& sx : plan->s_x)
+    if (sx) cudaStreamDestroy(sx);
+  if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+  for (auto& ev : plan->ev_unpacked)
+    if (ev) cudaEventDestroy(ev);
+  for (auto& ev : plan->ev_x_done)
+    if (ev) cudaEventDestroy(ev);
+  plan->s_unpack = nullptr;
+  plan->s_x[0] = plan->s_x[1] = nullptr;
   if (plan->acc) cudaFree(plan->acc);
   if (plan->planes) cudaFree(plan->planes);
   if (plan->status) cudaFree(plan->status);
@@ -63,6 +75,108 @@ void release(xcorr_plan plan) {
 namespace xc {
 xcorr_status set_error(xcorr_status st, const std::string& msg) { return fail(st, msg); }
 }  // namespace xc
+
+namespace {
+
+xcorr_status check_execute(xcorr_plan plan, const void* d_in, int n_time) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  if (!d_in) return fail(XCORR_ERR_INVALID_ARG, "d_in is NULL");
+  if (n_time < 1 || n_time > plan->cfg.max_time_per_exec)
+    return fail(XCORR_ERR_INVALID_ARG, "n_time must be in [1, max_time_per_exec]");
+  if (plan->samples + n_time > plan->max_integration)
+    return fail(XCORR_ERR_OVERFLOW, "the integration would exceed " + std::to_string(plan->max_integration) +
+                                        " samples, the exact int32 bound; dump with reset first");
+  return XCORR_OK;
+}
+
+// Channel groups for the tensor path: enough tile pairs per group for about
+// four waves of the persistent X kernel, at most kMaxGroups.
+int tensor_groups(xcorr_plan plan) {
+  const int nb = (plan->n_inputs + 127) / 128;
+  const int64_t items = (int64_t)plan->cfg.n_channels * nb * (nb + 1) / 2;
+  int64_t g = items / (4LL * plan->num_sms);
+  if (g > xc::kMaxGroups) g = xc::kMaxGroups;
+  if (g > plan->cfg.n_channels) g = plan->cfg.n_channels;
+  return g < 1 ? 1 : static_cast<int>(g);
+}
+
+// Correlate n_time samples into target (the plan's accumulator, or the
+// caller's buffer for a fused dump).  target_fresh: store instead of add.
+xcorr_status run_execute(xcorr_plan plan, const void* d_in, int n_time, int2* target, bool target_fresh,
+                         cudaStream_t s) {
+  const int C = plan->cfg.n_channels, N = plan->n_inputs;
+  cudaError_t e;
+  cudaEvent_t* ev = nullptr;
+  if (plan->prof_cap) {
+    const int64_t slot = plan->prof_count % plan->prof_cap;
+    ev = plan->prof_events + xc::kProfileEvents * slot;
+    if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return cuda_fail(e, "profile event");
+  }
+  if (plan->engine == XCORR_ENGINE_TENSOR) {
+    if (plan->tmap_ntime != n_time) {
+      std::string err;
+      if (!xc::encode_plane_tmap(&plan->tmap, plan->planes, N, plan->ni_pad, n_time, plan->cfg.max_time_per_exec, C,
+                                 &err))
+        return fail(XCORR_ERR_CUDA, err);
+      plan->tmap_ntime = n_time;
+    }
+    const int G = tensor_groups(plan);
+    const int per = (C + G - 1) / G;
+    // fork: both internal streams start after everything queued on s so far
+    if ((e = cudaEventRecord(plan->ev_fork, s)) != cudaSuccess) return cuda_fail(e, "fork event");
+    if ((e = cudaStreamWaitEvent(plan->s_unpack, plan->ev_fork, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(plan->s_x[0], plan->ev_fork, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(plan->s_x[1], plan->ev_fork, 0)) != cudaSuccess)
+      return cuda_fail(e, "fork wait");
+    const uint8_t* in = static_cast<const uint8_t*>(d_in);
+    int used = 0;
+    for (int g = 0, c0 = 0; c0 < C; ++g, c0 += per) {
+      const int nc = (C - c0 < per) ? C - c0 : per;
+      // unpack channels [c0, c0 + nc) of every time row (the rows stay C channels apart)
+      e = xc::launch_unpack_ci4_e4m3_channels(in, plan->planes, n_time, C, c0, nc, N, plan->ni_pad,
+                                              plan->cfg.max_time_per_exec, plan->num_sms, plan->s_unpack);
+      if (e != cudaSuccess) return cuda_fail(e, "unpack launch");
+      if ((e = cudaEventRecord(plan->ev_unpacked[g], plan->s_unpack)) != cudaSuccess) return cuda_fail(e, "event");
+      cudaStream_t sx = plan->s_x[g & 1];
+      if ((e = cudaStreamWaitEvent(sx, plan->ev_unpacked[g], 0)) != cudaSuccess) return cuda_fail(e, "wait");
+      if (ev && (e = cudaEventRecord(ev[2 + 2 * g], sx)) != cudaSuccess) return cuda_fail(e, "profile event");
+      e = xc::launch_xcorr_tc_e4m3(&plan->tmap, n_time, c0, nc, N, target, !target_fresh, plan->status,
+                                   plan->num_sms, sx);
+      if (e != cudaSuccess) return cuda_fail(e, "tensor-core X kernel launch");
+      if (ev && (e = cudaEventRecord(ev[3 + 2 * g], sx)) != cudaSuccess) return cuda_fail(e, "profile event");
+      used = g + 1;
+    }
+    if (ev && (e = cudaEventRecord(ev[1], plan->s_unpack)) != cudaSuccess) return cuda_fail(e, "profile event");
+    // join: s continues after both X streams (which waited for every unpack)
+    for (int k = 0; k < 2; ++k) {
+      if ((e = cudaEventRecord(plan->ev_x_done[k], plan->s_x[k])) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(s, plan->ev_x_done[k], 0)) != cudaSuccess)
+        return cuda_fail(e, "join");
+    }
+    if (ev) plan->prof_ngroups[plan->prof_count % plan->prof_cap] = used;
+  } else {
+    const int ks = xc::cuda_core_ksplit(n_time, C, N, plan->num_sms);
+    int mode = target_fresh ? xc::MODE_STORE : xc::MODE_ADD;
+    if (ks > 1) {
+      if (target_fresh) {
+        e = cudaMemsetAsync(target, 0, (size_t)C * plan->n_pairs * sizeof(int2), s);
+        if (e != cudaSuccess) return cuda_fail(e, "accumulator clear");
+      }
+      mode = xc::MODE_ATOMIC;
+    }
+    if (ev && ((e = cudaEventRecord(ev[1], s)) != cudaSuccess || (e = cudaEventRecord(ev[2], s)) != cudaSuccess))
+      return cuda_fail(e, "profile event");
+    e = xc::launch_xcorr_cuda_core(plan->cfg.fmt, d_in, n_time, C, N, target, mode, ks, s);
+    if (e != cudaSuccess) return cuda_fail(e, "CUDA-core X kernel launch");
+    if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return cuda_fail(e, "profile event");
+    if (ev) plan->prof_ngroups[plan->prof_count % plan->prof_cap] = 1;
+  }
+  if (ev) ++plan->prof_count;
+  return XCORR_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -141,6 +255,19 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
                 std::string("device allocation failed: ") + cudaGetErrorString(e));
   }
   *plan->status_host = 0;
+  if (engine == XCORR_ENGINE_TENSOR) {
+    e = cudaStreamCreateWithFlags(&plan->s_unpack, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&plan->s_x[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming);
+    for (int k = 0; k < xc::kMaxGroups && e == cudaSuccess; ++k)
+      e = cudaEventCreateWithFlags(&plan->ev_unpacked[k], cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&plan->ev_x_done[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      release(plan);
+      delete plan;
+      return cuda_fail(e, "stream or event creation");
+    }
+  }
   if ((e = cudaMemset(plan->status, 0, 256)) != cudaSuccess ||
       (e = cudaDeviceSynchronize()) != cudaSuccess) {
     release(plan);
@@ -152,56 +279,35 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
 }
 
 xcorr_status xcorr_execute(xcorr_plan plan, const void* d_in, int n_time, void* stream) {
-  xcorr_status st = plan_ok(plan);
+  xcorr_status st = check_execute(plan, d_in, n_time);
   if (st != XCORR_OK) return st;
-  if (!d_in) return fail(XCORR_ERR_INVALID_ARG, "d_in is NULL");
-  if (n_time < 1 || n_time > plan->cfg.max_time_per_exec)
-    return fail(XCORR_ERR_INVALID_ARG, "n_time must be in [1, max_time_per_exec]");
-  if (plan->samples + n_time > plan->max_integration)
-    return fail(XCORR_ERR_OVERFLOW, "the integration would exceed " + std::to_string(plan->max_integration) +
-                                        " samples, the exact int32 bound; dump with reset first");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int C = plan->cfg.n_channels, N = plan->n_inputs;
-  cudaError_t e;
-  cudaEvent_t* ev = nullptr;
-  if (plan->prof_cap) {
-    ev = plan->prof_events + 3 * (plan->prof_count % plan->prof_cap);
-    if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return cuda_fail(e, "profile event");
-  }
-  if (plan->engine == XCORR_ENGINE_TENSOR) {
-    e = xc::launch_unpack_ci4_e4m3(static_cast<const uint8_t*>(d_in), plan->planes, n_time, C, N, plan->ni_pad,
-                                   plan->cfg.max_time_per_exec, plan->num_sms, s);
-    if (e != cudaSuccess) return cuda_fail(e, "unpack launch");
-    if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "profile event");
-    if (plan->tmap_ntime != n_time) {
-      std::string err;
-      if (!xc::encode_plane_tmap(&plan->tmap, plan->planes, N, plan->ni_pad, n_time, plan->cfg.max_time_per_exec,
-                                 C, &err))
-        return fail(XCORR_ERR_CUDA, err);
-      plan->tmap_ntime = n_time;
-    }
-    e = xc::launch_xcorr_tc_e4m3(&plan->tmap, n_time, C, N, plan->acc, !plan->fresh, plan->status, plan->num_sms, s);
-    if (e != cudaSuccess) return cuda_fail(e, "tensor-core X kernel launch");
-  } else {
-    const int ks = xc::cuda_core_ksplit(n_time, C, N, plan->num_sms);
-    int mode = plan->fresh ? xc::MODE_STORE : xc::MODE_ADD;
-    if (ks > 1) {
-      if (plan->fresh) {
-        e = cudaMemsetAsync(plan->acc, 0, (size_t)C * plan->n_pairs * sizeof(int2), s);
-        if (e != cudaSuccess) return cuda_fail(e, "accumulator clear");
-      }
-      mode = xc::MODE_ATOMIC;
-    }
-    if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return cuda_fail(e, "profile event");
-    e = xc::launch_xcorr_cuda_core(plan->cfg.fmt, d_in, n_time, C, N, plan->acc, mode, ks, s);
-    if (e != cudaSuccess) return cuda_fail(e, "CUDA-core X kernel launch");
-  }
-  if (ev) {
-    if ((e = cudaEventRecord(ev[2], s)) != cudaSuccess) return cuda_fail(e, "profile event");
-    ++plan->prof_count;
-  }
+  st = run_execute(plan, d_in, n_time, plan->acc, plan->fresh, static_cast<cudaStream_t>(stream));
+  if (st != XCORR_OK) return st;
   plan->samples += n_time;
   plan->fresh = false;
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_execute_dump(xcorr_plan plan, const void* d_in, int n_time, void* out, int out_on_device,
+                                unsigned flags, void* stream, int64_t* n_samples) {
+  xcorr_status st = check_execute(plan, d_in, n_time);
+  if (st != XCORR_OK) return st;
+  if (!out) return fail(XCORR_ERR_INVALID_ARG, "out is NULL");
+  if (flags & ~(XCORR_DUMP_RESET | XCORR_DUMP_ADD_WIDE)) return fail(XCORR_ERR_INVALID_ARG, "unknown dump flag");
+  const bool direct = plan->fresh && (flags & XCORR_DUMP_RESET) && !(flags & XCORR_DUMP_ADD_WIDE) && out_on_device;
+  if (!direct) {
+    st = xcorr_execute(plan, d_in, n_time, stream);
+    if (st != XCORR_OK) return st;
+    return xcorr_dump(plan, out, out_on_device, flags, stream, n_samples);
+  }
+  // This execute is the whole integration and it is not kept: the X kernel
+  // writes it straight into the caller's buffer and the plan stays reset.
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = run_execute(plan, d_in, n_time, static_cast<int2*>(out), true, s);
+  if (st != XCORR_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(plan->status_host, plan->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  if (n_samples) *n_samples = n_time;
   return XCORR_OK;
 }
 
@@ -266,19 +372,25 @@ xcorr_status xcorr_plan_query(xcorr_plan plan, xcorr_plan_info* info) {
   info->max_integration = plan->max_integration;
   info->device_bytes = plan->device_bytes;
   info->output_bytes = (size_t)plan->cfg.n_channels * plan->n_pairs * sizeof(int2);
+  info->kernels_per_execute = plan->engine == XCORR_ENGINE_TENSOR ? 2 * tensor_groups(plan) : 1;
   return XCORR_OK;
 }
 
 xcorr_status xcorr_profile_enable(xcorr_plan plan, int capacity) {
   xcorr_status st = plan_ok(plan);
   if (st != XCORR_OK) return st;
-  if (capacity < 0 || capacity > (1 << 20)) return fail(XCORR_ERR_INVALID_ARG, "capacity must be in [0, 2^20]");
+  if (capacity < 0 || capacity > (1 << 16)) return fail(XCORR_ERR_INVALID_ARG, "capacity must be in [0, 65536]");
   free_profile(plan);
   if (capacity == 0) return XCORR_OK;
-  plan->prof_events = new (std::nothrow) cudaEvent_t[3 * (size_t)capacity]();
-  if (!plan->prof_events) return fail(XCORR_ERR_OOM, "host allocation failed");
+  const int64_t n = (int64_t)xc::kProfileEvents * capacity;
+  plan->prof_events = new (std::nothrow) cudaEvent_t[n]();
+  plan->prof_ngroups = new (std::nothrow) int[capacity]();
+  if (!plan->prof_events || !plan->prof_ngroups) {
+    free_profile(plan);
+    return fail(XCORR_ERR_OOM, "host allocation failed");
+  }
   plan->prof_cap = capacity;
-  for (int k = 0; k < 3 * capacity; ++k) {
+  for (int64_t k = 0; k < n; ++k) {
     cudaError_t e = cudaEventCreate(&plan->prof_events[k]);
     if (e != cudaSuccess) {
       free_profile(plan);
@@ -297,12 +409,21 @@ xcorr_status xcorr_profile_read(xcorr_plan plan, float* ms, int capacity, int* c
   const int64_t have = plan->prof_count < plan->prof_cap ? plan->prof_count : plan->prof_cap;
   const int64_t n = have < capacity ? have : capacity;
   for (int64_t k = 0; k < n; ++k) {
-    const int64_t launch = plan->prof_count - n + k;
-    cudaEvent_t* ev = plan->prof_events + 3 * (launch % plan->prof_cap);
-    cudaError_t e = cudaEventSynchronize(ev[2]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[2 * k], ev[0], ev[1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[2 * k + 1], ev[1], ev[2]);
+    const int64_t slot = (plan->prof_count - n + k) % plan->prof_cap;
+    cudaEvent_t* ev = plan->prof_events + xc::kProfileEvents * slot;
+    const int groups = plan->prof_ngroups[slot];
+    float unpack = 0.f, x = 0.f;
+    cudaError_t e = cudaEventSynchronize(ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&unpack, ev[0], ev[1]);
+    for (int g = 0; g < groups && e == cudaSuccess; ++g) {
+      float d = 0.f;
+      e = cudaEventSynchronize(ev[3 + 2 * g]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&d, ev[2 + 2 * g], ev[3 + 2 * g]);
+      x += d;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "profile read");
+    ms[2 * k] = unpack;
+    ms[2 * k + 1] = x;
   }
   *count = static_cast<int>(n);
   return XCORR_OK;

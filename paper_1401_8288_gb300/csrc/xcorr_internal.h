@@ -19,11 +19,19 @@ constexpr int64_t kMaxIntegrationCI8 = (INT64_C(2147483647)) / 32768;  // 65,535
 
 // The tensor path accumulates E4M3 products in FP32 tensor memory, exact while
 // every partial sum stays below 2^24: at most 128 * W for a window of W
-// samples.  1023 stages of 128 samples keep 128 * W = 16,760,832 < 2^24.
-constexpr int kTcStageT = 128;
-constexpr int kTcMaxKblocksPerWindow = 1023;
+// samples.  W = 130,944 keeps 128 * W = 16,760,832 < 2^24.
+constexpr int kTcStageT = 64;  // samples per pipeline stage (TMA box height)
+constexpr int kTcWindowSamples = 130944;
+constexpr int kTcMaxKblocksPerWindow = kTcWindowSamples / kTcStageT;
+static_assert(kTcWindowSamples % kTcStageT == 0, "window must hold whole stages");
 
 enum ExecMode : int { MODE_STORE = 0, MODE_ADD = 1, MODE_ATOMIC = 2 };
+
+// The tensor path splits the channels of an execute into groups: the unpack
+// of group g + 1 runs on one internal stream while the X kernel of group g
+// runs on another, so the HBM-bound unpack hides under the tensor-bound X.
+constexpr int kMaxGroups = 8;
+constexpr int kProfileEvents = 2 + 2 * kMaxGroups;  // per timed execute
 
 }  // namespace xc
 
@@ -50,9 +58,19 @@ struct xcorr_plan_s {
   CUtensorMap tmap{};  // planes, for the n_time of the last tensor execute
   int tmap_ntime = -1;
 
-  cudaEvent_t* prof_events = nullptr;  // 3 per timed execute (xcorr_profile_enable)
+  // internal streams of the tensor path (forked from and joined to the caller's stream)
+  cudaStream_t s_unpack = nullptr;
+  cudaStream_t s_x[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_unpacked[xc::kMaxGroups] = {};
+  cudaEvent_t ev_x_done[2] = {nullptr, nullptr};
+
+  // timing (xcorr_profile_enable): kProfileEvents per timed execute -- start,
+  // end of the last unpack, then (begin, end) of each X launch
+  cudaEvent_t* prof_events = nullptr;
   int prof_cap = 0;
   int64_t prof_count = 0;
+  int* prof_ngroups = nullptr;  // groups used by each timed execute
 };
 
 namespace xc {
@@ -61,10 +79,16 @@ namespace xc {
 cudaError_t launch_unpack_ci4_e4m3(const uint8_t* in, uint8_t* planes, int n_time, int n_chan,
                                    int n_inputs, int ni_pad, int max_time, int num_sms,
                                    cudaStream_t stream);
+// The same for channels [c0, c0 + nc) only.
+cudaError_t launch_unpack_ci4_e4m3_channels(const uint8_t* in, uint8_t* planes, int n_time, int n_chan,
+                                            int c0, int nc, int n_inputs, int ni_pad, int max_time,
+                                            int num_sms, cudaStream_t stream);
 
-cudaError_t launch_xcorr_tc_e4m3(const CUtensorMap* tmap, int n_time, int n_chan, int n_inputs,
-                                 int2* acc, bool accumulate, int* status, int num_sms,
-                                 cudaStream_t stream);
+// Channels [chan0, chan0 + n_chan) of the planes described by tmap; acc points
+// at channel 0 of the packed accumulator.
+cudaError_t launch_xcorr_tc_e4m3(const CUtensorMap* tmap, int n_time, int chan0, int n_chan,
+                                 int n_inputs, int2* acc, bool accumulate, int* status,
+                                 int num_sms, cudaStream_t stream);
 
 cudaError_t launch_xcorr_cuda_core(int fmt, const void* in, int n_time, int n_chan, int n_inputs,
                                    int2* acc, int mode, int ksplit, cudaStream_t stream);

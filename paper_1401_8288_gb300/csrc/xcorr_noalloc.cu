@@ -93,7 +93,8 @@ extern "C" xcorr_status xcorr_correlate_ci4_noalloc(const void* d_in, int n_time
   std::string err;
   if (!xc::encode_plane_tmap(&tmap, plane_buf, n_inputs, ni_pad, n_time, n_time, n_channels, &err))
     return xc::set_error(XCORR_ERR_CUDA, err);
-  e = xc::launch_xcorr_tc_e4m3(&tmap, n_time, n_channels, n_inputs, static_cast<int2*>(d_out), false, status, n_sms, s);
+  e = xc::launch_xcorr_tc_e4m3(&tmap, n_time, 0, n_channels, n_inputs, static_cast<int2*>(d_out), false, status,
+                               n_sms, s);
   if (e != cudaSuccess)
     return xc::set_error(XCORR_ERR_CUDA, std::string("X kernel launch: ") + cudaGetErrorString(e));
   if (d_status) {

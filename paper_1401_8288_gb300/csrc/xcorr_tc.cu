@@ -8,9 +8,9 @@
 //
 // The input triangle is cut into 128 x 128 tile pairs (I >= J); a persistent
 // CTA walks a static list of (channel, I, J) items, channel-major, so the
-// CTAs in flight share the channels' planes in L2.  Per 128-sample stage, TMA
-// brings the four 128 x 128 E4M3 tiles Xr_I, Xi_I, Xr_J, Xi_J (two on the
-// diagonal) into shared memory as MN-major operands, and one thread issues,
+// CTAs in flight share the channels' planes in L2.  Per 64-sample stage, TMA
+// brings the four 64 x 128 E4M3 tiles Xr_I, Xi_I, Xr_J, Xi_J (two on the
+// diagonal) into a six-deep shared-memory ring as MN-major operands, and one thread issues,
 // per 32-sample step, three MMAs into an FP32 accumulator of 256 TMEM columns
 // holding [Re | -Im]:
 //     [Re | -Im] += Xr_I [Xr_J | Xi_J]^T       (M = 128, N = 256)
@@ -18,7 +18,7 @@
 //     -Im        += (-Xi_I) Xr_J^T             (N = 128, negate-A bit)
 // Every product is exact (4-bit integers are E4M3 values), and FP32 sums of
 // integers are exact below 2^24, so the K axis is cut into windows of at most
-// 1023 stages (128 * 130,944 < 2^24); each window is drained to int32.  Two
+// 130,944 samples (128 * 130,944 < 2^24); each window is drained to int32.  Two
 // accumulator buffers (512 columns) let the epilogue of one window overlap the
 // MMAs of the next.
 //
@@ -35,9 +35,9 @@ namespace {
 
 constexpr int kBlk = 128;                   // inputs per tile side
 constexpr int kKT = kTcStageT;              // samples per stage
-constexpr int kTileBytes = kBlk * kKT;      // one E4M3 plane tile: 16 KB
+constexpr int kTileBytes = kBlk * kKT;      // one E4M3 plane tile: 8 KB
 constexpr int kStageBytes = 4 * kTileBytes; // Xr_I, Xi_I, Xr_J, Xi_J
-constexpr int kStages = 3;
+constexpr int kStages = 6;
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 192;
 constexpr int kProducerWarp = 4;
@@ -52,7 +52,7 @@ constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kStagingBytes + kBarri
 static_assert(kSmemBytes <= 232448, "shared memory budget");
 
 struct TcParams {
-  int n_chan, n_inputs, n_tile_pairs, n_kblocks, kb_per_window;
+  int chan0, n_chan, n_inputs, n_tile_pairs, n_kblocks, kb_per_window;
   int64_t n_pairs;
   int accumulate_first;  // the first window adds into acc (else it stores)
   int2* acc;
@@ -108,12 +108,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       prefetch_tmap(&tmap);
       int s = 0;
-      uint32_t ph = 0, filled = 0, fill_parity[kStages] = {0, 0, 0};
+      uint32_t ph = 0, filled = 0, fill_parity[kStages] = {};
       bool ok = true;
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-        const int c = item / p.n_tile_pairs;
+        const int cl = item / p.n_tile_pairs;
+        const int c = p.chan0 + cl;
         int I, J;
-        tile_pair(item - c * p.n_tile_pairs, I, J);
+        tile_pair(item - cl * p.n_tile_pairs, I, J);
         const bool diag = (I == J);
         for (int kb = 0; kb < p.n_kblocks; ++kb) {
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
@@ -208,10 +209,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     int g = 0;
     bool ok = true;
     for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-      const int c = item / p.n_tile_pairs;
+      const int cl = item / p.n_tile_pairs;
       int I, J;
-      tile_pair(item - c * p.n_tile_pairs, I, J);
-      int2* acc_c = p.acc + (int64_t)c * p.n_pairs;
+      tile_pair(item - cl * p.n_tile_pairs, I, J);
+      int2* acc_c = p.acc + (int64_t)(p.chan0 + cl) * p.n_pairs;
       const int row0 = I * kBlk + warp * 32;  // first global input row of this warp
       for (int w = 0; w < n_windows; ++w, ++g) {
         const int buf = g & 1;
@@ -273,9 +274,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace
 
-cudaError_t launch_xcorr_tc_e4m3(const CUtensorMap* tmap, int n_time, int n_chan, int n_inputs,
-                                 int2* acc, bool accumulate, int* status, int num_sms,
-                                 cudaStream_t stream) {
+cudaError_t launch_xcorr_tc_e4m3(const CUtensorMap* tmap, int n_time, int chan0, int n_chan,
+                                 int n_inputs, int2* acc, bool accumulate, int* status,
+                                 int num_sms, cudaStream_t stream) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(xcorr_tc_e4m3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -285,6 +286,7 @@ cudaError_t launch_xcorr_tc_e4m3(const CUtensorMap* tmap, int n_time, int n_chan
   }
   const int nb = (n_inputs + kBlk - 1) / kBlk;
   TcParams p;
+  p.chan0 = chan0;
   p.n_chan = n_chan;
   p.n_inputs = n_inputs;
   p.n_tile_pairs = nb * (nb + 1) / 2;

@@ -40,19 +40,20 @@ __device__ __forceinline__ void ci4_to_e4m3(uint32_t v, uint32_t& re, uint32_t& 
   im = e4m3_of_nibbles(v & 0x07070707u, ((v >> 3) & 0x01010101u) * 0xFFu);
 }
 
-// 16 inputs of one (t, c) row per thread; grid-stride over all rows.
-__global__ void __launch_bounds__(256) unpack_ci4_e4m3_vec(const uint4* __restrict__ in,
+// Channels [c0, c0 + nc) of every time row, 16 inputs per thread (N_i a
+// multiple of 16 and a 16-byte aligned input); grid-stride over the rows.
+__global__ void __launch_bounds__(256) unpack_ci4_e4m3_vec(const uint8_t* __restrict__ in,
                                                            uint8_t* __restrict__ planes, int64_t n_rows,
-                                                           int n_chan, int q_per_row, int ni_pad,
-                                                           int64_t comp_stride) {
+                                                           int n_chan, int c0, int nc, int q_per_row,
+                                                           int ni_pad, int64_t comp_stride) {
   const int64_t total = n_rows * q_per_row;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = q / q_per_row;  // row = t * n_chan + c
+    const int64_t row = q / q_per_row;  // row = t * nc + (c - c0)
     const int k = static_cast<int>(q - row * q_per_row);
-    const int64_t t = row / n_chan;
-    const int c = static_cast<int>(row - t * n_chan);
-    const uint4 v = __ldg(in + q);
+    const int64_t t = row / nc;
+    const int c = c0 + static_cast<int>(row - t * nc);
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + ((t * n_chan + c) * q_per_row + k) * 16));
     uint4 r, m;
     ci4_to_e4m3(v.x, r.x, m.x);
     ci4_to_e4m3(v.y, r.y, m.y);
@@ -64,20 +65,20 @@ __global__ void __launch_bounds__(256) unpack_ci4_e4m3_vec(const uint4* __restri
   }
 }
 
-// Any even input count: one byte per thread.
+// Any input count and alignment: one byte per thread.
 __global__ void __launch_bounds__(256) unpack_ci4_e4m3_byte(const uint8_t* __restrict__ in,
                                                             uint8_t* __restrict__ planes,
-                                                            int64_t n_rows, int n_chan, int n_inputs,
-                                                            int ni_pad, int64_t comp_stride) {
+                                                            int64_t n_rows, int n_chan, int c0, int nc,
+                                                            int n_inputs, int ni_pad, int64_t comp_stride) {
   const int64_t total = n_rows * n_inputs;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = q / n_inputs;
     const int i = static_cast<int>(q - row * n_inputs);
-    const int64_t t = row / n_chan;
-    const int c = static_cast<int>(row - t * n_chan);
+    const int64_t t = row / nc;
+    const int c = c0 + static_cast<int>(row - t * nc);
     uint32_t re, im;
-    ci4_to_e4m3(in[q], re, im);
+    ci4_to_e4m3(in[(t * n_chan + c) * n_inputs + i], re, im);
     uint8_t* dst = planes + (2 * (int64_t)c) * comp_stride + t * ni_pad + i;
     dst[0] = static_cast<uint8_t>(re);
     dst[comp_stride] = static_cast<uint8_t>(im);
@@ -86,10 +87,10 @@ __global__ void __launch_bounds__(256) unpack_ci4_e4m3_byte(const uint8_t* __res
 
 }  // namespace
 
-cudaError_t launch_unpack_ci4_e4m3(const uint8_t* in, uint8_t* planes, int n_time, int n_chan,
-                                   int n_inputs, int ni_pad, int max_time, int num_sms,
-                                   cudaStream_t stream) {
-  const int64_t n_rows = (int64_t)n_time * n_chan;
+cudaError_t launch_unpack_ci4_e4m3_channels(const uint8_t* in, uint8_t* planes, int n_time, int n_chan,
+                                            int c0, int nc, int n_inputs, int ni_pad, int max_time,
+                                            int num_sms, cudaStream_t stream) {
+  const int64_t n_rows = (int64_t)n_time * nc;
   const int64_t comp_stride = (int64_t)max_time * ni_pad;
   const int threads = 256;
   const bool vec = (n_inputs % 16 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0);
@@ -99,12 +100,19 @@ cudaError_t launch_unpack_ci4_e4m3(const uint8_t* in, uint8_t* planes, int n_tim
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   if (vec)
-    unpack_ci4_e4m3_vec<<<(unsigned)blocks, threads, 0, stream>>>(
-        reinterpret_cast<const uint4*>(in), planes, n_rows, n_chan, n_inputs / 16, ni_pad, comp_stride);
+    unpack_ci4_e4m3_vec<<<(unsigned)blocks, threads, 0, stream>>>(in, planes, n_rows, n_chan, c0, nc,
+                                                                 n_inputs / 16, ni_pad, comp_stride);
   else
-    unpack_ci4_e4m3_byte<<<(unsigned)blocks, threads, 0, stream>>>(in, planes, n_rows, n_chan, n_inputs,
-                                                                  ni_pad, comp_stride);
+    unpack_ci4_e4m3_byte<<<(unsigned)blocks, threads, 0, stream>>>(in, planes, n_rows, n_chan, c0, nc,
+                                                                  n_inputs, ni_pad, comp_stride);
   return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_ci4_e4m3(const uint8_t* in, uint8_t* planes, int n_time, int n_chan,
+                                   int n_inputs, int ni_pad, int max_time, int num_sms,
+                                   cudaStream_t stream) {
+  return launch_unpack_ci4_e4m3_channels(in, planes, n_time, n_chan, 0, n_chan, n_inputs, ni_pad, max_time,
+                                         num_sms, stream);
 }
 
 // ------------------------------------------------------------ tensor map ---

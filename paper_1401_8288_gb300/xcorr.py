@@ -29,7 +29,8 @@ ENGINES = {"auto": XCORR_ENGINE_AUTO, "tensor": XCORR_ENGINE_TENSOR,
 
 EXPORTS = ("xcorr_plan_create", "xcorr_execute", "xcorr_dump", "xcorr_sync", "xcorr_plan_query",
            "xcorr_destroy", "xcorr_last_error", "xcorr_baseline_index", "xcorr_profile_enable",
-           "xcorr_profile_read", "xcorr_measure_peak", "xcorr_correlate_ci4_noalloc")
+           "xcorr_profile_read", "xcorr_measure_peak", "xcorr_correlate_ci4_noalloc",
+           "xcorr_execute_dump")
 PEAK_KINDS = {"tc_e4m3": 0, "tc_bf16": 1, "mma_sync_s8": 2, "dp4a": 3}
 
 
@@ -50,7 +51,8 @@ class xcorr_plan_info(ctypes.Structure):
     _fields_ = [("n_inputs", ctypes.c_int), ("n_channels", ctypes.c_int),
                 ("n_pairs", ctypes.c_int64), ("engine", ctypes.c_int),
                 ("samples_integrated", ctypes.c_int64), ("max_integration", ctypes.c_int64),
-                ("device_bytes", ctypes.c_size_t), ("output_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("output_bytes", ctypes.c_size_t),
+                ("kernels_per_execute", ctypes.c_int)]
 
 
 _lib = None
@@ -75,6 +77,7 @@ def load():
                 "xcorr_plan_create": [ctypes.POINTER(vp), ctypes.POINTER(xcorr_config)],
                 "xcorr_execute": [vp, vp, i, vp],
                 "xcorr_dump": [vp, vp, i, u, vp, ctypes.POINTER(i64)],
+                "xcorr_execute_dump": [vp, vp, i, vp, i, u, vp, ctypes.POINTER(i64)],
                 "xcorr_sync": [vp, vp],
                 "xcorr_plan_query": [vp, ctypes.POINTER(xcorr_plan_info)],
                 "xcorr_destroy": [vp],
@@ -120,6 +123,14 @@ def xcorr_execute(plan, d_in: int, n_time: int, stream: int = 0) -> None:
 def xcorr_dump(plan, out: int, out_on_device: bool, flags: int = 0, stream: int = 0) -> int:
     n = ctypes.c_int64()
     _check(load().xcorr_dump(plan, out, int(out_on_device), flags, stream, ctypes.byref(n)))
+    return n.value
+
+
+def xcorr_execute_dump(plan, d_in: int, n_time: int, out: int, out_on_device: bool,
+                       flags: int = XCORR_DUMP_RESET, stream: int = 0) -> int:
+    n = ctypes.c_int64()
+    _check(load().xcorr_execute_dump(plan, d_in, n_time, out, int(out_on_device), flags, stream,
+                                     ctypes.byref(n)))
     return n.value
 
 
@@ -214,6 +225,19 @@ class Plan:
         flags = (XCORR_DUMP_RESET if reset else 0) | (XCORR_DUMP_ADD_WIDE if wide else 0)
         self.samples = xcorr_dump(self.handle, out.data_ptr(), out.is_cuda, flags,
                                   self._stream(stream))
+        return out
+
+    def execute_dump(self, x, out=None, reset: bool = True, wide: bool = False, stream=None):
+        """execute(x) then dump(...), fused into one pass when x is the whole integration."""
+        torch = self._torch
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("input must be a contiguous CUDA tensor")
+        if out is None:
+            out = torch.zeros((self.n_channels, self.info["n_pairs"], 2),
+                              dtype=torch.int64 if wide else torch.int32, device="cuda")
+        flags = (XCORR_DUMP_RESET if reset else 0) | (XCORR_DUMP_ADD_WIDE if wide else 0)
+        self.samples = xcorr_execute_dump(self.handle, x.data_ptr(), x.shape[0], out.data_ptr(),
+                                          out.is_cuda, flags, self._stream(stream))
         return out
 
     def sync(self, stream=None) -> None:

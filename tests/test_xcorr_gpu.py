@@ -154,6 +154,42 @@ def test_input_at_any_byte_offset(torch, engine, fmt):
         assert np.array_equal(got, want), off
 
 
+@pytest.mark.parametrize("n_chan", [500, 700])
+def test_tensor_channel_groups(torch, n_chan):
+    # 256 inputs (3 tile pairs per channel): 500 channels run as 2 groups of
+    # 250 and 700 channels as 3 groups (234, 234, 232), unpack and X
+    # overlapping on the plan's internal streams
+    x = synth.uniform_ci4(64, n_chan, 128, seed=n_chan, lo=-8, hi=7)
+    got, _ = run(torch, x, "tensor")
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_execute_dump_fused_and_plain(torch, engine):
+    x = synth.uniform_ci4(200, 3, 70, seed=77, lo=-8, hi=7)
+    y = synth.uniform_ci4(200, 3, 70, seed=78, lo=-8, hi=7)
+    want_x = oracle.correlate(oracle.FMT_CI4, x)
+    want_y = oracle.correlate(oracle.FMT_CI4, y)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    with xcorr.Plan(70, 3, 200, engine=engine) as plan:
+        a = plan.execute_dump(xd)                 # fused: straight into the output
+        b = plan.execute_dump(yd)                 # fused again: nothing leaks from x
+        plan.execute(xd)                          # an integration in progress ...
+        c = plan.execute_dump(yd)                 # ... so this one is execute + dump
+        d = plan.execute_dump(xd, reset=False)    # not reset: execute + dump, keeps integrating
+        e = plan.dump()
+        host = np.zeros_like(want_x, dtype=np.int32)
+        n = xcorr.xcorr_execute_dump(plan.handle, yd.data_ptr(), 200, host.ctypes.data, False,
+                                     xcorr.XCORR_DUMP_RESET, 0)  # host output: execute + dump
+        plan.sync()
+        torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy(), want_x)
+    assert np.array_equal(b.cpu().numpy(), want_y)
+    assert np.array_equal(c.cpu().numpy(), want_x + want_y)
+    assert np.array_equal(d.cpu().numpy(), want_x) and np.array_equal(e.cpu().numpy(), want_x)
+    assert n == 200 and np.array_equal(host, want_y)
+
+
 def test_ci8_cuda_core_full_code_range(torch):
     x = synth.uniform_ci8(150, 3, 37, seed=23)  # includes -128
     got, _ = run(torch, x, "cuda_core", fmt="ci8")
