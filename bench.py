@@ -34,8 +34,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("X-stage complex MACs/s and % of GB300 int8 tensor peak vs CUDA-core kernel, "
           "bit-exact")
-WORKLOAD = dict(name="512 inputs (256 stations x 2 pols), 512 channels, K=2048, 4+4-bit",
-                n_sta=256, n_chan=512, n_time=2048, seed=14018288 + 2)
+WORKLOADS = {
+    # the headline: 512 inputs, 4+4-bit Gaussian + plane wave
+    "ci4_512in": dict(name="512 inputs (256 stations x 2 pols), 512 channels, K=2048, 4+4-bit",
+                      n_sta=256, n_chan=512, n_time=2048, seed=14018288 + 2, fmt="ci4",
+                      gen="planewave", dtype="e4m3"),
+    # the small field-system-sized case: 64 inputs
+    "ci4_64in": dict(name="64 inputs (32 stations x 2 pols), 64 channels, K=1024, 4+4-bit",
+                     n_sta=32, n_chan=64, n_time=1024, seed=14018288 + 1, fmt="ci4",
+                     gen="uniform", dtype="e4m3"),
+    # the precision ladder at 512 inputs: int8 and float spectra
+    "ci8_512in": dict(name="512 inputs, 256 channels, K=4096, 8-bit complex (sigma 20)",
+                      n_sta=256, n_chan=256, n_time=4096, seed=14018288 + 3, fmt="ci8",
+                      gen="gauss8", dtype="bf16"),
+    "cf32_512in": dict(name="512 inputs, 256 channels, K=4096, float32 complex (sigma 1)",
+                       n_sta=256, n_chan=256, n_time=4096, seed=14018288 + 4, fmt="cf32",
+                       gen="gauss32", dtype="bf16x3"),
+}
+WORKLOAD = WORKLOADS["ci4_512in"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "xcorr_tc_e4m3_512in_512ch_2048t.json")
 
 
@@ -47,9 +63,13 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing on the host cores")
-    ap.add_argument("--channels", type=int, default=WORKLOAD["n_chan"],
+    ap.add_argument("--channels", type=int, default=0,
                     help="channels per GPU (a smaller case of the same kernels, for profiler "
-                         "captures; the reported workload is 512)")
+                         "captures); 0 = the workload's own")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ci4_512in",
+                    help="the default is the headline 512-input 4-bit workload")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch shape")
     return ap.parse_args()
 
 
@@ -168,17 +188,18 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_sample(x, budget_s: float, n_pairs: int) -> dict:
+def oracle_sample(x, fmt: str, budget_s: float, n_pairs: int) -> dict:
     """Time the oracle, as it stands, on a bounded sample of the workload: whole
     channels, one per host core per round, until about budget_s of CPU time."""
     import oracle
+    ofmt = {"ci4": oracle.FMT_CI4, "ci8": oracle.FMT_CI8, "cf32": oracle.FMT_CF32}[fmt]
     cores = cpu_cores()
     n_time, n_chan = x.shape[0], x.shape[1]
     t0 = time.perf_counter()
     done = 0
     while done < n_chan:
         c1 = min(n_chan, done + cores)
-        oracle.correlate(oracle.FMT_CI4, x, c0=done, c1=c1, threads=cores)
+        oracle.correlate(ofmt, x, c0=done, c1=c1, threads=cores)
         done = c1
         if time.perf_counter() - t0 > budget_s:
             break
@@ -188,6 +209,18 @@ def oracle_sample(x, budget_s: float, n_pairs: int) -> dict:
             "sample": f"{done} of {n_chan} channels, all {n_pairs} pairs, K={n_time}"}
 
 
+def make_input(w: dict, seed: int):
+    from paper_1401_8288_gb300 import synth
+    args = (w["n_time"], w["n_chan"], w["n_sta"])
+    if w["gen"] == "planewave":
+        return synth.gaussian_planewave_ci4(*args, seed=seed)
+    if w["gen"] == "uniform":
+        return synth.uniform_ci4(*args, seed=seed)
+    if w["gen"] == "gauss8":
+        return synth.gaussian_ci8(*args, seed=seed)
+    return synth.gaussian_cf32(*args, seed=seed)
+
+
 # ------------------------------------------------------------ reference --
 def reference_arm(args) -> int:
     from paper_1401_8288_gb300 import dist
@@ -195,10 +228,11 @@ def reference_arm(args) -> int:
     if info.rank != 0:
         return 0  # the oracle arm runs on rank 0 alone
     import oracle
-    from paper_1401_8288_gb300 import costmodel, synth
+    from paper_1401_8288_gb300 import costmodel
     oracle.build()
-    w = WORKLOAD
-    x = synth.gaussian_planewave_ci4(w["n_time"], w["n_chan"], w["n_sta"], seed=w["seed"])
+    w = WORKLOADS[args.workload]
+    x = make_input(w, w["seed"])
+    ofmt = {"ci4": oracle.FMT_CI4, "ci8": oracle.FMT_CI8, "cf32": oracle.FMT_CF32}[w["fmt"]]
     n_pairs = costmodel.n_pairs(2 * w["n_sta"])
     cores = cpu_cores()
     per_step = max(1, cores)  # channels per step: one per host core
@@ -207,7 +241,7 @@ def reference_arm(args) -> int:
         c0 = (k * per_step) % w["n_chan"]
         c1 = min(w["n_chan"], c0 + per_step)
         t0 = time.perf_counter()
-        oracle.correlate(oracle.FMT_CI4, x, c0=c0, c1=c1, threads=cores)
+        oracle.correlate(ofmt, x, c0=c0, c1=c1, threads=cores)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append((c1 - c0, dt))
@@ -218,7 +252,8 @@ def reference_arm(args) -> int:
     emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "TCMAC/s",
           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
           "ms_per_step": 1e3 * total_s / max(1, len(times)), "higher_is_better": True,
-          "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+          "scaling": "weak", "vs_baseline": None,
+          "dtype": "f64" if w["fmt"] == "cf32" else "int64", "data": "synthetic",
           "config": {"workload": w["name"], "sample": sample},
           "cpu_baseline": {"value": value, "unit": "TCMAC/s", "cores": cores, "kind": "oracle",
                            "sample": sample},
@@ -238,25 +273,27 @@ def our_arm(args) -> int:
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_1401_8288_gb300 import costmodel, synth, xcorr
+    from paper_1401_8288_gb300 import costmodel, xcorr
 
-    w = dict(WORKLOAD)
-    if args.channels != w["n_chan"]:
+    w = dict(WORKLOADS[args.workload])
+    if args.channels and args.channels != w["n_chan"]:
+        w["name"] = w["name"].replace(f"{w['n_chan']} channels", f"{args.channels} channels")
         w["n_chan"] = args.channels
-        w["name"] = w["name"].replace("512 channels", f"{args.channels} channels")
-    n_sta, n_chan, n_time = w["n_sta"], w["n_chan"], w["n_time"]
+    n_sta, n_chan, n_time, fmt = w["n_sta"], w["n_chan"], w["n_time"], w["fmt"]
     n_in = 2 * n_sta
     n_pairs = costmodel.n_pairs(n_in)
     cmacs_per_step = costmodel.cmacs(n_chan, n_time, n_in)
-    # rank r correlates channel band r of a world * 512-channel observation
-    x = synth.gaussian_planewave_ci4(n_time, n_chan, n_sta, seed=w["seed"] + info.rank)
+    # rank r correlates channel band r of a world * n_chan-channel observation
+    x = make_input(w, w["seed"] + info.rank)
     x_pin = torch.from_numpy(x).pin_memory()
     xd = x_pin.to(dev)
     in_bytes, out_bytes = x.nbytes, n_chan * n_pairs * 8
 
-    plan = xcorr.Plan(n_sta, n_chan, n_time, fmt="ci4", engine="tensor")
-    launches_per_step = plan.info["kernels_per_execute"]  # unpack + X launches per channel group
-    out = torch.empty((n_chan, n_pairs, 2), dtype=torch.int32, device=dev)
+    plan = xcorr.Plan(n_sta, n_chan, n_time, fmt=fmt, engine="tensor")
+    tuning, tune_ms = (plan.query()["tuning"], None) if args.no_autotune else plan.autotune(xd)
+    launches_per_step = plan.query()["kernels_per_execute"]  # unpack + X launches per channel group
+    out_dtype = torch.float32 if fmt == "cf32" else torch.int32
+    out = torch.empty((n_chan, n_pairs, 2), dtype=out_dtype, device=dev)
 
     def step():
         plan.execute_dump(xd, out, reset=True)
@@ -283,7 +320,7 @@ def our_arm(args) -> int:
     value = info.world * cmacs_per_step * args.steps / (ms_total * 1e-3) / 1e12
 
     # end to end through the public API: pinned host input -> device -> X-stage -> host result
-    host_out = torch.empty((n_chan, n_pairs, 2), dtype=torch.int32).pin_memory()
+    host_out = torch.empty((n_chan, n_pairs, 2), dtype=out_dtype).pin_memory()
 
     def e2e_step():
         xd.copy_(x_pin, non_blocking=True)
@@ -301,20 +338,20 @@ def our_arm(args) -> int:
     e2e_ms = dist.max_over_ranks(ev0.elapsed_time(ev1), dev)
     e2e_value = info.world * cmacs_per_step * args.steps / (e2e_ms * 1e-3) / 1e12
 
-    # the plain CUDA-core kernel on the same workload
-    cc_steps = max(2, min(args.steps, 5))
-    with xcorr.Plan(n_sta, n_chan, n_time, fmt="ci4", engine="cuda_core") as cc:
-        cc.execute(xd)
-        cc.dump(out, reset=True)
-        torch.cuda.synchronize()
-        ev0.record()
-        for _ in range(cc_steps):
-            cc.execute(xd)
-            cc.dump(out, reset=True)
-        ev1.record()
-        torch.cuda.synchronize()
-        cc_ms = ev0.elapsed_time(ev1) / cc_steps
-    cc_value = cmacs_per_step / (cc_ms * 1e-3) / 1e12
+    # the plain CUDA-core kernel on the same workload (integer formats)
+    cc_value = cc_ms = None
+    if fmt != "cf32":
+        cc_steps = max(2, min(args.steps, 5))
+        with xcorr.Plan(n_sta, n_chan, n_time, fmt=fmt, engine="cuda_core") as cc:
+            cc.execute_dump(xd, out)
+            torch.cuda.synchronize()
+            ev0.record()
+            for _ in range(cc_steps):
+                cc.execute_dump(xd, out)
+            ev1.record()
+            torch.cuda.synchronize()
+            cc_ms = ev0.elapsed_time(ev1) / cc_steps
+        cc_value = cmacs_per_step / (cc_ms * 1e-3) / 1e12
     plan.close()
 
     # measured arithmetic peaks of this device
@@ -324,16 +361,20 @@ def our_arm(args) -> int:
 
     x_ms = statistics.mean(k for _, k in kernel_ms)
     unpack_ms = statistics.mean(u for u, _ in kernel_ms)
-    ops_per_launch = costmodel.int8_ops(n_chan, n_time, n_in)
-    achieved = ops_per_launch / (x_ms * 1e-3) / 1e12
+    # algorithmic work of one step: 8 operations per complex MAC, six times
+    # that for the float path (its algorithm is six BF16 piece products)
+    split = 6 if fmt == "cf32" else 1
+    ops_per_step = split * costmodel.int8_ops(n_chan, n_time, n_in)
+    achieved = ops_per_step / (x_ms * 1e-3) / 1e12
     peaks = measured_peaks()
+    ratio = 2.0 if fmt == "ci4" else 1.0  # E4M3 runs at twice the BF16 rate
     if "bf16_tflops" in peaks:
-        peak = 2.0 * peaks["bf16_tflops"]
-        peak_note = ("E4M3 dense = 2 x measured bf16 burst (MEASURED_PEAKS.json) by the nominal "
-                     "fp8:bf16 ratio; of measured")
+        peak = ratio * peaks["bf16_tflops"]
+        peak_note = (("E4M3 dense = 2 x " if ratio == 2 else "BF16 dense = ")
+                     + "measured bf16 burst (MEASURED_PEAKS.json); of measured")
     else:
-        peak = 2.0 * 1900.0
-        peak_note = "E4M3 dense = 2 x 1.9 PFLOP/s bf16; of fallback"
+        peak = ratio * 1900.0
+        peak_note = "bf16 1.9 PFLOP/s x fp8:bf16 ratio; of fallback"
 
     result = {
         "metric": METRIC,
@@ -346,21 +387,32 @@ def our_arm(args) -> int:
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "e4m3",
+        "dtype": w["dtype"],
         "data": "synthetic",
         "config": {"workload": w["name"],
-                   "input": "4+4-bit complex, Gaussian sigma 2.5 levels + common plane wave 0.3 sigma",
-                   "engine": "tcgen05 kind::f8f6f4 (E4M3 codes of 4-bit integers, exact FP32 "
-                             "TMEM sums drained to int32)",
+                   "input": {"planewave": "4+4-bit complex, Gaussian sigma 2.5 levels + common "
+                                          "plane wave 0.3 sigma",
+                             "uniform": "4+4-bit complex, uniform integers in [-7, 7]",
+                             "gauss8": "int8 complex, Gaussian sigma 20 clipped to +-127",
+                             "gauss32": "float32 complex, Gaussian sigma 1"}[w["gen"]],
+                   "engine": {"ci4": "tcgen05 kind::f8f6f4 (E4M3 codes of 4-bit integers, exact "
+                                     "FP32 TMEM sums drained to int32)",
+                              "ci8": "tcgen05 kind::f16 (BF16 copies of int8 values, exact FP32 "
+                                     "sums drained to int32 every 384 samples)",
+                              "cf32": "tcgen05 kind::f16 (three BF16 pieces per value, six piece "
+                                      "products, FP32 sums drained every 384 samples)"}[fmt],
+                   "tuning": tuning,
                    "l2": f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB in, "
                          f"{out_bytes / 1e6:.0f} MB out per step)",
                    "parallelism": f"frequency bands x{info.world}",
                    "cmacs_per_step_per_gpu": cmacs_per_step},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": stored_traffic(),
-                     "kernel": "xcorr_tc_e4m3_kernel", "ops_per_launch": ops_per_launch,
-                     "kernel_ms": x_ms, "peak_source": peak_note,
-                     "frac_of_probe_e4m3": achieved / peak_e4m3},
+                     "frac": achieved / peak,
+                     "traffic": stored_traffic() if args.workload == "ci4_512in" else None,
+                     "kernel": "xcorr_tc_kernel", "ops_per_step": ops_per_step,
+                     "launches_per_step": launches_per_step // 2, "kernel_ms_per_step": x_ms,
+                     "peak_source": peak_note,
+                     "frac_of_probe_peak": achieved / (peak_e4m3 if fmt == "ci4" else peak_e4m3 / 2)},
         "e2e": {"value": e2e_value, "unit": "TCMAC/s", "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": out_bytes, "ms_per_step": e2e_ms / args.steps},
         "gpu_launches": launches_per_step * args.steps,
@@ -370,14 +422,15 @@ def our_arm(args) -> int:
         "peaks_measured_tops": {"tcgen05_e4m3": peak_e4m3, "mma_sync_s8": peak_s8,
                                 "dp4a": peak_dp4a},
         "cuda_core": {"value": cc_value, "unit": "TCMAC/s", "ms_per_step": cc_ms,
-                      "speedup_tensor_vs_cuda_core": value / info.world / cc_value},
+                      "speedup_tensor_vs_cuda_core": (value / info.world / cc_value)
+                      if cc_value else None},
         "kernels_ms": {"unpack_span": unpack_ms, "x_tensor_sum": x_ms,
                        "note": "per step: start to end of the last unpack, and the summed "
                                "durations of the X launches (channel groups overlap the "
                                "unpack of the next group with the X kernel of this one)"},
     }
     if info.rank == 0 and info.world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = oracle_sample(x, budget_s=12.0, n_pairs=n_pairs)
+        result["cpu_baseline"] = oracle_sample(x, fmt, budget_s=12.0, n_pairs=n_pairs)
     if info.rank == 0:
         emit(result)
     dist.barrier()

@@ -23,7 +23,13 @@
  *                  for each component"; the nibble order is this library's
  *                  reading, the paper does not fix it).
  *   XCORR_IN_CI8   int8 pair (re, im), the unpacked 8-bit form of Sec. 2.4.
- *   XCORR_IN_CF32  float pair (re, im), spectra from a GPU F-stage (Sec. 1).
+ *   XCORR_IN_CF32  float pair (re, im), spectra from a GPU F-stage (Sec. 1);
+ *                  finite values, magnitudes in [2^-60, 2^60].  Each input's
+ *                  samples are quantised per 384-sample window against the
+ *                  window's largest magnitude (23 bits) and split into three
+ *                  integer digits; the six leading digit products are summed
+ *                  exactly per window and scaled into a float accumulator.
+ *                  The error is about 1e-7 of sqrt(|V_ii V_jj|) per entry.
  *
  * Output layout: the packed lower triangle per channel, pair index
  * p(i, j) = i (i + 1) / 2 + j for i >= j, (re, im) interleaved:
@@ -82,6 +88,13 @@ typedef struct {
 
 typedef struct xcorr_plan_s *xcorr_plan;
 
+/* Launch shape of the tensor-core path (xcorr_plan_set_tuning, xcorr_autotune). */
+typedef struct {
+    int stage_variant;  /* shared-memory ring: 0 = 3 x 64 KB, 1 = 4 x 48 KB, 2 = 6 x 32 KB stages */
+    int groups;         /* channel groups whose unpack overlaps the X kernel; 0 = automatic (<= 8) */
+    int x_streams;      /* 1 or 2 streams the groups' X launches alternate over                 */
+} xcorr_tuning;
+
 /* Opaque to the caller except through these fields (xcorr_plan_query). */
 typedef struct {
     int n_inputs;             /* N_i = 2 * n_stations                                    */
@@ -93,14 +106,21 @@ typedef struct {
     size_t device_bytes;      /* device memory the plan owns                             */
     size_t output_bytes;      /* bytes of one dump in the plan's own element type        */
     int kernels_per_execute;  /* kernel launches of one full-size execute (unpack + X)   */
+    xcorr_tuning tuning;      /* current launch shape (groups resolved)                  */
 } xcorr_plan_info;
 
 /*
  * Create a plan.  Validates cfg, allocates the device accumulator and any
  * staging buffers on the current device (the plan owns them), and selects the
  * kernels.  *out receives the plan, or NULL on failure.
+ * Engines: AUTO and TENSOR use the tcgen05 kernels for every format (4-bit as
+ * E4M3, int8 as BF16, float as three BF16 pieces); CUDA_CORE takes CI4 / CI8.
+ * max_integration (xcorr_plan_query) is 16,777,215 samples for CI4, 65,535
+ * for CI8 (exact int32) and 16,777,216 for CF32 (longer sums: dump with
+ * XCORR_DUMP_ADD_WIDE into double).
  * Errors: INVALID_ARG (bad sizes, n_pols != 2, NULL pointers), UNSUPPORTED
- * (no GB300-class device, or CF32 with the CUDA-core engine), BUDGET, OOM, CUDA.
+ * (no GB300-class device, or CF32 with the CUDA-core engine), OVERFLOW
+ * (max_time_per_exec beyond max_integration), BUDGET, OOM, CUDA.
  */
 xcorr_status xcorr_plan_create(xcorr_plan *out, const xcorr_config *cfg);
 
@@ -149,6 +169,23 @@ xcorr_status xcorr_execute_dump(xcorr_plan plan, const void *d_in, int n_time, v
 
 /* Wait for the stream and report any kernel-side failure (DEVICE). */
 xcorr_status xcorr_sync(xcorr_plan plan, void *stream);
+
+/*
+ * Fix the tensor path's launch shape (results do not depend on it).
+ * Errors: INVALID_ARG (stage_variant not in [0, 2], groups not in [0, 8],
+ * x_streams not 1 or 2), DEVICE.
+ */
+xcorr_status xcorr_plan_set_tuning(xcorr_plan plan, const xcorr_tuning *tuning);
+
+/*
+ * Autotuner: time every launch shape of the tensor path on this input (three
+ * runs each, the first as warm-up), keep the fastest on the plan and return it
+ * in *best (and its time in ms in *best_ms; either may be NULL).  Discards the
+ * plan's current integration.  Synchronises the stream.  A CUDA-core plan has
+ * nothing to tune and returns at once.  Errors: INVALID_ARG, CUDA, DEVICE.
+ */
+xcorr_status xcorr_autotune(xcorr_plan plan, const void *d_in, int n_time, void *stream,
+                            xcorr_tuning *best, float *best_ms);
 
 /* Describe the plan.  Errors: INVALID_ARG. */
 xcorr_status xcorr_plan_query(xcorr_plan plan, xcorr_plan_info *info);

@@ -1,5 +1,5 @@
 // xcorr_api.cu -- the C ABI (xcorr.h): plan validation, device memory owned
-// by the plan, kernel selection and stream-ordered launches.
+// by the plan, kernel selection, tuning and stream-ordered launches.
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -62,6 +62,8 @@ void release(xcorr_plan plan) {
   plan->s_x[0] = plan->s_x[1] = nullptr;
   if (plan->acc) cudaFree(plan->acc);
   if (plan->planes) cudaFree(plan->planes);
+  if (plan->exps) cudaFree(plan->exps);
+  plan->exps = nullptr;
   if (plan->status) cudaFree(plan->status);
   if (plan->status_host) cudaFreeHost(plan->status_host);
   plan->acc = nullptr;
@@ -69,14 +71,6 @@ void release(xcorr_plan plan) {
   plan->status = nullptr;
   plan->status_host = nullptr;
 }
-
-}  // namespace
-
-namespace xc {
-xcorr_status set_error(xcorr_status st, const std::string& msg) { return fail(st, msg); }
-}  // namespace xc
-
-namespace {
 
 xcorr_status check_execute(xcorr_plan plan, const void* d_in, int n_time) {
   xcorr_status st = plan_ok(plan);
@@ -86,24 +80,46 @@ xcorr_status check_execute(xcorr_plan plan, const void* d_in, int n_time) {
     return fail(XCORR_ERR_INVALID_ARG, "n_time must be in [1, max_time_per_exec]");
   if (plan->samples + n_time > plan->max_integration)
     return fail(XCORR_ERR_OVERFLOW, "the integration would exceed " + std::to_string(plan->max_integration) +
-                                        " samples, the exact int32 bound; dump with reset first");
+                                        " samples (the exact range of one dump); dump with reset first");
   return XCORR_OK;
 }
 
-// Channel groups for the tensor path: enough tile pairs per group for about
-// four waves of the persistent X kernel, at most kMaxGroups.
+// Channel groups of the tensor path: the tuned count, else enough tile pairs
+// per group for about four waves of the persistent X kernel.
 int tensor_groups(xcorr_plan plan) {
-  const int nb = (plan->n_inputs + 127) / 128;
-  const int64_t items = (int64_t)plan->cfg.n_channels * nb * (nb + 1) / 2;
-  int64_t g = items / (4LL * plan->num_sms);
+  int64_t g;
+  if (plan->tune_groups > 0) {
+    g = plan->tune_groups;
+  } else {
+    const int nb = (plan->n_inputs + 127) / 128;
+    const int64_t items = (int64_t)plan->cfg.n_channels * nb * (nb + 1) / 2;
+    g = items / (4LL * plan->num_sms);
+  }
   if (g > xc::kMaxGroups) g = xc::kMaxGroups;
   if (g > plan->cfg.n_channels) g = plan->cfg.n_channels;
   return g < 1 ? 1 : static_cast<int>(g);
 }
 
+// Unpack channels [c0, c0 + nc) of the input into the plan's planes.
+cudaError_t unpack_group(xcorr_plan plan, const void* d_in, int n_time, int c0, int nc, cudaStream_t s) {
+  const int C = plan->cfg.n_channels, N = plan->n_inputs, T = plan->cfg.max_time_per_exec;
+  switch (plan->cfg.fmt) {
+    case XCORR_IN_CI4:
+      return xc::launch_unpack_ci4_e4m3_channels(static_cast<const uint8_t*>(d_in), static_cast<uint8_t*>(plan->planes),
+                                                 n_time, C, c0, nc, N, plan->ni_pad, T, plan->num_sms, s);
+    case XCORR_IN_CI8:
+      return xc::launch_unpack_ci8_bf16(static_cast<const int8_t*>(d_in), static_cast<uint16_t*>(plan->planes), n_time,
+                                        C, c0, nc, N, plan->ni_pad, T, plan->num_sms, s);
+    default:
+      return xc::launch_unpack_cf32_digits(static_cast<const float*>(d_in), static_cast<uint16_t*>(plan->planes),
+                                           plan->exps, n_time, C, c0, nc, N, plan->ni_pad, T, plan->window_samples,
+                                           plan->exp_windows, s);
+  }
+}
+
 // Correlate n_time samples into target (the plan's accumulator, or the
 // caller's buffer for a fused dump).  target_fresh: store instead of add.
-xcorr_status run_execute(xcorr_plan plan, const void* d_in, int n_time, int2* target, bool target_fresh,
+xcorr_status run_execute(xcorr_plan plan, const void* d_in, int n_time, void* target, bool target_fresh,
                          cudaStream_t s) {
   const int C = plan->cfg.n_channels, N = plan->n_inputs;
   cudaError_t e;
@@ -114,36 +130,62 @@ xcorr_status run_execute(xcorr_plan plan, const void* d_in, int n_time, int2* ta
     if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return cuda_fail(e, "profile event");
   }
   if (plan->engine == XCORR_ENGINE_TENSOR) {
-    if (plan->tmap_ntime != n_time) {
+    const int variant = plan->tune_variant;
+    if (plan->tmap_ntime != n_time || plan->tmap_variant != variant) {
       std::string err;
-      if (!xc::encode_plane_tmap(&plan->tmap, plan->planes, N, plan->ni_pad, n_time, plan->cfg.max_time_per_exec, C,
-                                 &err))
+      if (!xc::encode_plane_tmap(&plan->tmap, plan->planes, plan->elem_bytes, N, plan->ni_pad, n_time,
+                                 plan->cfg.max_time_per_exec, C * plan->planes_per_chan,
+                                 xc::tc_stage_samples(plan->elem_bytes, variant), &err))
         return fail(XCORR_ERR_CUDA, err);
       plan->tmap_ntime = n_time;
+      plan->tmap_variant = variant;
     }
+    xc::TcLaunch L;
+    L.elem_bytes = plan->elem_bytes;
+    L.variant = variant;
+    L.float_out = plan->cfg.fmt == XCORR_IN_CF32;
+    L.n_time = n_time;
+    L.n_inputs = N;
+    L.planes_per_chan = plan->planes_per_chan;
+    if (plan->cfg.fmt == XCORR_IN_CF32) {
+      // the six digit products d_p d_q with p + q <= 2
+      L.exps = plan->exps;
+      L.exp_windows = plan->exp_windows;
+      L.ni_pad = plan->ni_pad;
+      const int pp[6] = {0, 0, 1, 0, 2, 1}, pq[6] = {0, 1, 0, 2, 0, 1};
+      L.n_pairs_k = 6;
+      for (int k = 0; k < 6; ++k) {
+        L.pair_p[k] = pp[k];
+        L.pair_q[k] = pq[k];
+      }
+    }
+    L.window_samples = plan->window_samples;
+    L.accumulate = !target_fresh;
+    L.out = target;
+    L.status = plan->status;
+    L.num_sms = plan->num_sms;
     const int G = tensor_groups(plan);
     const int per = (C + G - 1) / G;
-    // fork: both internal streams start after everything queued on s so far
+    const int nxs = plan->tune_x_streams == 1 ? 1 : 2;
+    // fork: the internal streams start after everything queued on s so far
     if ((e = cudaEventRecord(plan->ev_fork, s)) != cudaSuccess) return cuda_fail(e, "fork event");
     if ((e = cudaStreamWaitEvent(plan->s_unpack, plan->ev_fork, 0)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(plan->s_x[0], plan->ev_fork, 0)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(plan->s_x[1], plan->ev_fork, 0)) != cudaSuccess)
       return cuda_fail(e, "fork wait");
-    const uint8_t* in = static_cast<const uint8_t*>(d_in);
     int used = 0;
     for (int g = 0, c0 = 0; c0 < C; ++g, c0 += per) {
       const int nc = (C - c0 < per) ? C - c0 : per;
-      // unpack channels [c0, c0 + nc) of every time row (the rows stay C channels apart)
-      e = xc::launch_unpack_ci4_e4m3_channels(in, plan->planes, n_time, C, c0, nc, N, plan->ni_pad,
-                                              plan->cfg.max_time_per_exec, plan->num_sms, plan->s_unpack);
-      if (e != cudaSuccess) return cuda_fail(e, "unpack launch");
+      if ((e = unpack_group(plan, d_in, n_time, c0, nc, plan->s_unpack)) != cudaSuccess)
+        return cuda_fail(e, "unpack launch");
       if ((e = cudaEventRecord(plan->ev_unpacked[g], plan->s_unpack)) != cudaSuccess) return cuda_fail(e, "event");
-      cudaStream_t sx = plan->s_x[g & 1];
+      cudaStream_t sx = plan->s_x[g % nxs];
       if ((e = cudaStreamWaitEvent(sx, plan->ev_unpacked[g], 0)) != cudaSuccess) return cuda_fail(e, "wait");
       if (ev && (e = cudaEventRecord(ev[2 + 2 * g], sx)) != cudaSuccess) return cuda_fail(e, "profile event");
-      e = xc::launch_xcorr_tc_e4m3(&plan->tmap, n_time, c0, nc, N, target, !target_fresh, plan->status,
-                                   plan->num_sms, sx);
-      if (e != cudaSuccess) return cuda_fail(e, "tensor-core X kernel launch");
+      L.chan0 = c0;
+      L.n_chan = nc;
+      if ((e = xc::launch_xcorr_tc(&plan->tmap, L, sx)) != cudaSuccess)
+        return cuda_fail(e, "tensor-core X kernel launch");
       if (ev && (e = cudaEventRecord(ev[3 + 2 * g], sx)) != cudaSuccess) return cuda_fail(e, "profile event");
       used = g + 1;
     }
@@ -167,7 +209,7 @@ xcorr_status run_execute(xcorr_plan plan, const void* d_in, int n_time, int2* ta
     }
     if (ev && ((e = cudaEventRecord(ev[1], s)) != cudaSuccess || (e = cudaEventRecord(ev[2], s)) != cudaSuccess))
       return cuda_fail(e, "profile event");
-    e = xc::launch_xcorr_cuda_core(plan->cfg.fmt, d_in, n_time, C, N, target, mode, ks, s);
+    e = xc::launch_xcorr_cuda_core(plan->cfg.fmt, d_in, n_time, C, N, static_cast<int2*>(target), mode, ks, s);
     if (e != cudaSuccess) return cuda_fail(e, "CUDA-core X kernel launch");
     if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return cuda_fail(e, "profile event");
     if (ev) plan->prof_ngroups[plan->prof_count % plan->prof_cap] = 1;
@@ -177,6 +219,10 @@ xcorr_status run_execute(xcorr_plan plan, const void* d_in, int n_time, int2* ta
 }
 
 }  // namespace
+
+namespace xc {
+xcorr_status set_error(xcorr_status st, const std::string& msg) { return fail(st, msg); }
+}  // namespace xc
 
 extern "C" {
 
@@ -197,16 +243,15 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
   if (c.engine != XCORR_ENGINE_AUTO && c.engine != XCORR_ENGINE_TENSOR && c.engine != XCORR_ENGINE_CUDA_CORE)
     return fail(XCORR_ERR_INVALID_ARG, "unknown engine");
 
-  int engine = c.engine;
-  if (c.fmt == XCORR_IN_CF32)
-    return fail(XCORR_ERR_UNSUPPORTED, "the float input path is not available in this build");
-  if (engine == XCORR_ENGINE_AUTO) engine = (c.fmt == XCORR_IN_CI4) ? XCORR_ENGINE_TENSOR : XCORR_ENGINE_CUDA_CORE;
-  if (engine == XCORR_ENGINE_TENSOR && c.fmt != XCORR_IN_CI4)
-    return fail(XCORR_ERR_UNSUPPORTED, "the tensor-core engine takes 4-bit input in this build");
+  const int engine = c.engine == XCORR_ENGINE_AUTO ? XCORR_ENGINE_TENSOR : c.engine;
+  if (engine == XCORR_ENGINE_CUDA_CORE && c.fmt == XCORR_IN_CF32)
+    return fail(XCORR_ERR_UNSUPPORTED, "the CUDA-core engine takes integer input only");
 
-  const int64_t max_int = (c.fmt == XCORR_IN_CI4) ? xc::kMaxIntegrationCI4 : xc::kMaxIntegrationCI8;
+  const int64_t max_int = c.fmt == XCORR_IN_CI4   ? xc::kMaxIntegrationCI4
+                          : c.fmt == XCORR_IN_CI8 ? xc::kMaxIntegrationCI8
+                                                  : xc::kMaxIntegrationCF32;
   if (c.max_time_per_exec > max_int)
-    return fail(XCORR_ERR_OVERFLOW, "max_time_per_exec exceeds the exact int32 integration bound of " +
+    return fail(XCORR_ERR_OVERFLOW, "max_time_per_exec exceeds the range of one integration, " +
                                         std::to_string(max_int) + " samples");
 
   int dev = 0;
@@ -222,10 +267,16 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
   const int n_inputs = 2 * c.n_stations;
   const int ni_pad = (n_inputs + 15) / 16 * 16;
   const int64_t n_pairs = n_pairs_of(n_inputs);
-  const size_t acc_bytes = (size_t)c.n_channels * (size_t)n_pairs * sizeof(int2);
-  const size_t planes_bytes =
-      engine == XCORR_ENGINE_TENSOR ? (size_t)c.n_channels * 2 * (size_t)c.max_time_per_exec * ni_pad : 0;
-  const size_t dev_bytes = acc_bytes + planes_bytes + 256;
+  const int elem_bytes = c.fmt == XCORR_IN_CI4 ? 1 : 2;
+  const int ppc = c.fmt == XCORR_IN_CF32 ? 6 : 2;
+  const size_t acc_bytes = (size_t)c.n_channels * (size_t)n_pairs * 8;
+  const size_t planes_bytes = engine == XCORR_ENGINE_TENSOR ? (size_t)c.n_channels * ppc *
+                                                                  (size_t)c.max_time_per_exec * ni_pad * elem_bytes
+                                                            : 0;
+  const int exp_windows = (c.max_time_per_exec + xc::kTcWindowBF16 - 1) / xc::kTcWindowBF16;
+  const size_t exps_bytes =
+      (engine == XCORR_ENGINE_TENSOR && c.fmt == XCORR_IN_CF32) ? (size_t)c.n_channels * exp_windows * ni_pad : 0;
+  const size_t dev_bytes = acc_bytes + planes_bytes + exps_bytes + 256;
   if (c.hbm_budget_bytes && dev_bytes > c.hbm_budget_bytes)
     return fail(XCORR_ERR_BUDGET, "plan needs " + std::to_string(dev_bytes) + " device bytes, budget is " +
                                       std::to_string(c.hbm_budget_bytes));
@@ -243,9 +294,14 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
   plan->max_integration = max_int;
   plan->planes_bytes = planes_bytes;
   plan->device_bytes = dev_bytes;
+  plan->elem_bytes = elem_bytes;
+  plan->planes_per_chan = ppc;
+  plan->window_samples = c.fmt == XCORR_IN_CI4 ? xc::kTcWindowCI4 : xc::kTcWindowBF16;
+  plan->exp_windows = exp_windows;
 
   if ((e = cudaMalloc(&plan->acc, acc_bytes)) != cudaSuccess ||
       (planes_bytes && (e = cudaMalloc(&plan->planes, planes_bytes)) != cudaSuccess) ||
+      (exps_bytes && (e = cudaMalloc(&plan->exps, exps_bytes)) != cudaSuccess) ||
       (e = cudaMalloc(&plan->status, 256)) != cudaSuccess ||
       (e = cudaMallocHost(&plan->status_host, sizeof(int))) != cudaSuccess) {
     release(plan);
@@ -268,8 +324,7 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
       return cuda_fail(e, "stream or event creation");
     }
   }
-  if ((e = cudaMemset(plan->status, 0, 256)) != cudaSuccess ||
-      (e = cudaDeviceSynchronize()) != cudaSuccess) {
+  if ((e = cudaMemset(plan->status, 0, 256)) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
     release(plan);
     delete plan;
     return cuda_fail(e, "plan initialisation");
@@ -288,6 +343,45 @@ xcorr_status xcorr_execute(xcorr_plan plan, const void* d_in, int n_time, void* 
   return XCORR_OK;
 }
 
+xcorr_status xcorr_dump(xcorr_plan plan, void* out, int out_on_device, unsigned flags, void* stream,
+                        int64_t* n_samples) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  if (!out) return fail(XCORR_ERR_INVALID_ARG, "out is NULL");
+  if (flags & ~(XCORR_DUMP_RESET | XCORR_DUMP_ADD_WIDE)) return fail(XCORR_ERR_INVALID_ARG, "unknown dump flag");
+  const bool wide = (flags & XCORR_DUMP_ADD_WIDE) != 0;
+  if (wide && !out_on_device) return fail(XCORR_ERR_INVALID_ARG, "XCORR_DUMP_ADD_WIDE needs device memory");
+  if (wide && reinterpret_cast<uintptr_t>(out) % 16)
+    return fail(XCORR_ERR_INVALID_ARG, "the wide output must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t total = (int64_t)plan->cfg.n_channels * plan->n_pairs;
+  const size_t bytes = (size_t)total * 8;
+  cudaError_t e;
+  if (plan->fresh) {  // nothing integrated since the last reset: the integration is zero
+    e = cudaMemsetAsync(plan->acc, 0, bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "accumulator clear");
+    plan->fresh = false;
+  }
+  if (wide) {
+    if (plan->cfg.fmt == XCORR_IN_CF32)
+      e = xc::launch_fold_wide_f64(static_cast<const float2*>(plan->acc), static_cast<double*>(out), total, s);
+    else
+      e = xc::launch_fold_wide_i64(static_cast<const int2*>(plan->acc), static_cast<int64_t*>(out), total, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fold launch");
+  } else {
+    e = cudaMemcpyAsync(out, plan->acc, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "dump copy");
+  }
+  e = cudaMemcpyAsync(plan->status_host, plan->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  if (n_samples) *n_samples = plan->samples;
+  if (flags & XCORR_DUMP_RESET) {
+    plan->samples = 0;
+    plan->fresh = true;
+  }
+  return XCORR_OK;
+}
+
 xcorr_status xcorr_execute_dump(xcorr_plan plan, const void* d_in, int n_time, void* out, int out_on_device,
                                 unsigned flags, void* stream, int64_t* n_samples) {
   xcorr_status st = check_execute(plan, d_in, n_time);
@@ -303,47 +397,11 @@ xcorr_status xcorr_execute_dump(xcorr_plan plan, const void* d_in, int n_time, v
   // This execute is the whole integration and it is not kept: the X kernel
   // writes it straight into the caller's buffer and the plan stays reset.
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  st = run_execute(plan, d_in, n_time, static_cast<int2*>(out), true, s);
+  st = run_execute(plan, d_in, n_time, out, true, s);
   if (st != XCORR_OK) return st;
   cudaError_t e = cudaMemcpyAsync(plan->status_host, plan->status, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(e, "status copy");
   if (n_samples) *n_samples = n_time;
-  return XCORR_OK;
-}
-
-xcorr_status xcorr_dump(xcorr_plan plan, void* out, int out_on_device, unsigned flags, void* stream,
-                        int64_t* n_samples) {
-  xcorr_status st = plan_ok(plan);
-  if (st != XCORR_OK) return st;
-  if (!out) return fail(XCORR_ERR_INVALID_ARG, "out is NULL");
-  if (flags & ~(XCORR_DUMP_RESET | XCORR_DUMP_ADD_WIDE)) return fail(XCORR_ERR_INVALID_ARG, "unknown dump flag");
-  const bool wide = (flags & XCORR_DUMP_ADD_WIDE) != 0;
-  if (wide && !out_on_device) return fail(XCORR_ERR_INVALID_ARG, "XCORR_DUMP_ADD_WIDE needs device memory");
-  if (wide && reinterpret_cast<uintptr_t>(out) % 16)
-    return fail(XCORR_ERR_INVALID_ARG, "the wide output must be 16-byte aligned");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int64_t total = (int64_t)plan->cfg.n_channels * plan->n_pairs;
-  const size_t bytes = (size_t)total * sizeof(int2);
-  cudaError_t e;
-  if (plan->fresh) {  // nothing integrated since the last reset: the integration is zero
-    e = cudaMemsetAsync(plan->acc, 0, bytes, s);
-    if (e != cudaSuccess) return cuda_fail(e, "accumulator clear");
-    plan->fresh = false;
-  }
-  if (wide) {
-    e = xc::launch_fold_wide_i64(plan->acc, static_cast<int64_t*>(out), total, s);
-    if (e != cudaSuccess) return cuda_fail(e, "fold launch");
-  } else {
-    e = cudaMemcpyAsync(out, plan->acc, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e, "dump copy");
-  }
-  e = cudaMemcpyAsync(plan->status_host, plan->status, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cuda_fail(e, "status copy");
-  if (n_samples) *n_samples = plan->samples;
-  if (flags & XCORR_DUMP_RESET) {
-    plan->samples = 0;
-    plan->fresh = true;
-  }
   return XCORR_OK;
 }
 
@@ -371,8 +429,92 @@ xcorr_status xcorr_plan_query(xcorr_plan plan, xcorr_plan_info* info) {
   info->samples_integrated = plan->samples;
   info->max_integration = plan->max_integration;
   info->device_bytes = plan->device_bytes;
-  info->output_bytes = (size_t)plan->cfg.n_channels * plan->n_pairs * sizeof(int2);
+  info->output_bytes = (size_t)plan->cfg.n_channels * plan->n_pairs * 8;
   info->kernels_per_execute = plan->engine == XCORR_ENGINE_TENSOR ? 2 * tensor_groups(plan) : 1;
+  info->tuning.stage_variant = plan->tune_variant;
+  info->tuning.groups = tensor_groups(plan);
+  info->tuning.x_streams = plan->tune_x_streams;
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_plan_set_tuning(xcorr_plan plan, const xcorr_tuning* t) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  if (!t) return fail(XCORR_ERR_INVALID_ARG, "tuning is NULL");
+  if (t->stage_variant < 0 || t->stage_variant >= xc::kTcVariants)
+    return fail(XCORR_ERR_INVALID_ARG, "stage_variant must be in [0, 2]");
+  if (t->groups < 0 || t->groups > xc::kMaxGroups) return fail(XCORR_ERR_INVALID_ARG, "groups must be in [0, 8]");
+  if (t->x_streams != 1 && t->x_streams != 2) return fail(XCORR_ERR_INVALID_ARG, "x_streams must be 1 or 2");
+  plan->tune_variant = t->stage_variant;
+  plan->tune_groups = t->groups;
+  plan->tune_x_streams = t->x_streams;
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_autotune(xcorr_plan plan, const void* d_in, int n_time, void* stream, xcorr_tuning* best,
+                            float* best_ms) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  if (!d_in || n_time < 1 || n_time > plan->cfg.max_time_per_exec)
+    return fail(XCORR_ERR_INVALID_ARG, "d_in must be set and n_time in [1, max_time_per_exec]");
+  if (plan->engine != XCORR_ENGINE_TENSOR) {  // nothing to tune
+    if (best) *best = xcorr_tuning{plan->tune_variant, plan->tune_groups, plan->tune_x_streams};
+    if (best_ms) *best_ms = 0.f;
+    return XCORR_OK;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  const int saved_cap = plan->prof_cap;
+  plan->prof_cap = 0;  // candidates are not profiled
+  const int group_choices[] = {1, 2, 4, 8};
+  xcorr_tuning winner{plan->tune_variant, plan->tune_groups, plan->tune_x_streams};
+  float winner_ms = 1e30f;
+  for (int v = 0; v < xc::kTcVariants && st == XCORR_OK; ++v) {
+    for (int gi = 0; gi < 4 && st == XCORR_OK; ++gi) {
+      for (int xs = 1; xs <= 2 && st == XCORR_OK; ++xs) {
+        if (group_choices[gi] == 1 && xs == 2) continue;  // one group has one X launch
+        plan->tune_variant = v;
+        plan->tune_groups = group_choices[gi];
+        plan->tune_x_streams = xs;
+        float best_rep = 1e30f;
+        for (int rep = 0; rep < 3 && st == XCORR_OK; ++rep) {  // the first run warms up
+          cudaEventRecord(e0, s);
+          st = run_execute(plan, d_in, n_time, plan->acc, true, s);
+          cudaEventRecord(e1, s);
+          if (st != XCORR_OK) break;
+          if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+            st = cuda_fail(e, "autotune timing");
+            break;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0 && ms < best_rep) best_rep = ms;
+        }
+        if (st == XCORR_OK && best_rep < winner_ms) {
+          winner_ms = best_rep;
+          winner = xcorr_tuning{v, group_choices[gi], xs};
+        }
+      }
+    }
+  }
+  plan->prof_cap = saved_cap;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the candidates overwrote the accumulator: the plan starts a new integration
+  plan->samples = 0;
+  plan->fresh = true;
+  plan->tune_variant = winner.stage_variant;
+  plan->tune_groups = winner.groups;
+  plan->tune_x_streams = winner.x_streams;
+  if (st != XCORR_OK) return st;
+  if (best) *best = winner;
+  if (best_ms) *best_ms = winner_ms;
   return XCORR_OK;
 }
 

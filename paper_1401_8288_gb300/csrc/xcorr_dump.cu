@@ -35,7 +35,28 @@ __global__ void fold_wide_i64_tail(const int2* __restrict__ acc, longlong2* __re
   }
 }
 
+// Float visibilities: widen each dump into a double running sum, the FP64
+// cross-dump accumulation for integrations longer than one FP32 dump.
+__global__ void __launch_bounds__(256) fold_wide_f64_kernel(const float2* __restrict__ acc,
+                                                            double2* __restrict__ out, int64_t n) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const float2 a = __ldg(acc + q);
+    double2 o = out[q];
+    o.x += a.x;
+    o.y += a.y;
+    out[q] = o;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_fold_wide_f64(const float2* acc, double* out, int64_t n_pairs_total, cudaStream_t stream) {
+  int64_t blocks = (n_pairs_total + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  if (blocks < 1) blocks = 1;
+  fold_wide_f64_kernel<<<(unsigned)blocks, 256, 0, stream>>>(acc, reinterpret_cast<double2*>(out), n_pairs_total);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fold_wide_i64(const int2* acc, int64_t* out, int64_t n_pairs_total, cudaStream_t stream) {
   const int64_t n4 = n_pairs_total / 2;

@@ -17,13 +17,18 @@ namespace xc {
 constexpr int64_t kMaxIntegrationCI4 = (INT64_C(2147483647)) / 128;    // 16,777,215
 constexpr int64_t kMaxIntegrationCI8 = (INT64_C(2147483647)) / 32768;  // 65,535
 
-// The tensor path accumulates E4M3 products in FP32 tensor memory, exact while
-// every partial sum stays below 2^24: at most 128 * W for a window of W
-// samples.  W = 130,944 keeps 128 * W = 16,760,832 < 2^24.
-constexpr int kTcStageT = 64;  // samples per pipeline stage (TMA box height)
-constexpr int kTcWindowSamples = 130944;
-constexpr int kTcMaxKblocksPerWindow = kTcWindowSamples / kTcStageT;
-static_assert(kTcWindowSamples % kTcStageT == 0, "window must hold whole stages");
+// The tensor path accumulates exact products in FP32 tensor memory and drains
+// it every window.  Integer input stays exact while every partial sum of a
+// window is an integer below 2^24: per sample at most 128 (4-bit) or 32768
+// (int8) per accumulator, so windows of 130,944 (4-bit: 16,760,832) and 384
+// (int8: 12,582,912) samples.  Float input is quantised per 384-sample window
+// into integer digits whose products are at most 2^14 (2 * 384 * 2^14 < 2^24).
+// Windows are multiples of every stage height (128, 96, 64 rows for E4M3;
+// 64, 48, 32 for BF16).
+constexpr int kTcWindowCI4 = 130944;
+constexpr int kTcWindowBF16 = 384;
+constexpr int kTcVariants = 3;  // stage shapes: 64 KB x 3, 48 KB x 4, 32 KB x 6
+constexpr int64_t kMaxIntegrationCF32 = INT64_C(16777216);  // FP32 per dump, widen beyond
 
 enum ExecMode : int { MODE_STORE = 0, MODE_ADD = 1, MODE_ATOMIC = 2 };
 
@@ -48,15 +53,26 @@ struct xcorr_plan_s {
   bool fresh = true;    // the accumulator holds nothing of the current integration
   int sticky = 0;       // a kernel failure was seen: every call fails until destroy
 
-  int2* acc = nullptr;         // [C][P] (re, im) int32
-  uint8_t* planes = nullptr;   // tensor path: E4M3 planes [C][2][max_time][ni_pad]
+  void* acc = nullptr;         // [C][P] (re, im): int32 (integer input) or float (float input)
+  void* planes = nullptr;      // tensor path: [C][planes_per_chan][max_time][ni_pad] numbers
+  int8_t* exps = nullptr;      // float input: window exponents [C][exp_windows][ni_pad]
+  int exp_windows = 0;
   size_t planes_bytes = 0;
+  int elem_bytes = 1;          // plane numbers: 1 = E4M3, 2 = BF16
+  int planes_per_chan = 2;     // re pieces then im pieces
+  int window_samples = 0;      // drain window of the tensor X kernel
   int* status = nullptr;       // device status word
   int* status_host = nullptr;  // pinned mirror, refreshed by every dump
   size_t device_bytes = 0;
 
-  CUtensorMap tmap{};  // planes, for the n_time of the last tensor execute
+  // tuning of the tensor path (xcorr_plan_set_tuning / xcorr_autotune); 0 = automatic
+  int tune_variant = 0;        // stage shape, 0 .. kTcVariants - 1
+  int tune_groups = 0;         // channel groups, 0 = heuristic
+  int tune_x_streams = 2;      // X launches alternate over 1 or 2 streams
+
+  CUtensorMap tmap{};          // planes, for tmap_ntime / tmap_variant
   int tmap_ntime = -1;
+  int tmap_variant = -1;
 
   // internal streams of the tensor path (forked from and joined to the caller's stream)
   cudaStream_t s_unpack = nullptr;
@@ -86,9 +102,25 @@ cudaError_t launch_unpack_ci4_e4m3_channels(const uint8_t* in, uint8_t* planes, 
 
 // Channels [chan0, chan0 + n_chan) of the planes described by tmap; acc points
 // at channel 0 of the packed accumulator.
-cudaError_t launch_xcorr_tc_e4m3(const CUtensorMap* tmap, int n_time, int chan0, int n_chan,
-                                 int n_inputs, int2* acc, bool accumulate, int* status,
-                                 int num_sms, cudaStream_t stream);
+// One launch of the tensor-core X kernel over channels [chan0, chan0 + n_chan).
+struct TcLaunch {
+  int elem_bytes = 1;       // 1: E4M3 planes (kind::f8f6f4), 2: BF16 planes (kind::f16)
+  int variant = 0;          // stage shape, 0 .. kTcVariants - 1
+  bool float_out = false;   // float accumulator (float input) or exact int32
+  int n_time = 0, chan0 = 0, n_chan = 0, n_inputs = 0;
+  int planes_per_chan = 2;  // re planes then im planes: 2 (one piece) or 6 (three)
+  int n_pairs_k = 1;        // plane pairs on the virtual K axis
+  int pair_p[8] = {0}, pair_q[8] = {0};
+  int window_samples = kTcWindowCI4;  // samples per drained block
+  const int8_t* exps = nullptr;       // float input: window exponents [C][exp_windows][ni_pad]
+  int exp_windows = 0, ni_pad = 0;
+  bool accumulate = false;  // add into out (else the first block stores)
+  void* out = nullptr;      // int2 or float2 [C][P]
+  int* status = nullptr;
+  int num_sms = 0;
+};
+int tc_stage_samples(int elem_bytes, int variant);
+cudaError_t launch_xcorr_tc(const CUtensorMap* tmap, const TcLaunch& launch, cudaStream_t stream);
 
 cudaError_t launch_xcorr_cuda_core(int fmt, const void* in, int n_time, int n_chan, int n_inputs,
                                    int2* acc, int mode, int ksplit, cudaStream_t stream);
@@ -102,8 +134,20 @@ xcorr_status set_error(xcorr_status st, const std::string& msg);
 cudaError_t launch_fold_wide_i64(const int2* acc, int64_t* out, int64_t n_pairs_total,
                                  cudaStream_t stream);
 
-// Encode the 3-D tensor map over the E4M3 planes (dims: input, time, channel*2+component).
-bool encode_plane_tmap(CUtensorMap* map, void* planes, int n_inputs, int ni_pad, int n_time,
-                       int max_time, int n_chan, std::string* err);
+// Encode the 3-D tensor map over planes of elem_bytes-byte numbers (dims:
+// input, time, channel * planes_per_chan + plane), box 128 bytes x box_t rows.
+bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inputs, int ni_pad,
+                       int n_time, int max_time, int n_planes_total, int box_t, std::string* err);
+
+// int8 (re, im) samples -> two BF16 planes [c][2][t][ni_pad] (exact).
+cudaError_t launch_unpack_ci8_bf16(const int8_t* in, uint16_t* planes, int n_time, int n_chan, int c0,
+                                   int nc, int n_inputs, int ni_pad, int max_time, int num_sms,
+                                   cudaStream_t stream);
+// float (re, im) samples -> six BF16 planes [c][6][t][ni_pad] of integer digits
+// (re digits 0-2, im digits 0-2) and one exponent per (channel, window, input).
+cudaError_t launch_unpack_cf32_digits(const float* in, uint16_t* planes, int8_t* exps, int n_time, int n_chan,
+                                      int c0, int nc, int n_inputs, int ni_pad, int max_time, int window,
+                                      int exp_windows, cudaStream_t stream);
+cudaError_t launch_fold_wide_f64(const float2* acc, double* out, int64_t n_pairs_total, cudaStream_t stream);
 
 }  // namespace xc

@@ -91,10 +91,22 @@ extern "C" xcorr_status xcorr_correlate_ci4_noalloc(const void* d_in, int n_time
   if (e != cudaSuccess) return xc::set_error(XCORR_ERR_CUDA, std::string("unpack launch: ") + cudaGetErrorString(e));
   CUtensorMap tmap;
   std::string err;
-  if (!xc::encode_plane_tmap(&tmap, plane_buf, n_inputs, ni_pad, n_time, n_time, n_channels, &err))
+  if (!xc::encode_plane_tmap(&tmap, plane_buf, 1, n_inputs, ni_pad, n_time, n_time, 2 * n_channels,
+                             xc::tc_stage_samples(1, 0), &err))
     return xc::set_error(XCORR_ERR_CUDA, err);
-  e = xc::launch_xcorr_tc_e4m3(&tmap, n_time, 0, n_channels, n_inputs, static_cast<int2*>(d_out), false, status,
-                               n_sms, s);
+  xc::TcLaunch L;
+  L.elem_bytes = 1;
+  L.variant = 0;
+  L.n_time = n_time;
+  L.chan0 = 0;
+  L.n_chan = n_channels;
+  L.n_inputs = n_inputs;
+  L.window_samples = xc::kTcWindowCI4;
+  L.accumulate = false;
+  L.out = d_out;
+  L.status = status;
+  L.num_sms = n_sms;
+  e = xc::launch_xcorr_tc(&tmap, L, s);
   if (e != cudaSuccess)
     return xc::set_error(XCORR_ERR_CUDA, std::string("X kernel launch: ") + cudaGetErrorString(e));
   if (d_status) {

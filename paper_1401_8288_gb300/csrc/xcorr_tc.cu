@@ -6,57 +6,92 @@
 //     Re V = Xr Xr^T + Xi Xi^T,   Im V = Xi Xr^T - Xr Xi^T
 // with X[i][t] the N_i x K matrix of one channel's samples.
 //
+// The operands are planes of tensor-core numbers, [channel][plane][t][input]:
+//   * 4-bit samples: two E4M3 planes (re, im); every code in [-8, 7] is exact;
+//   * int8 samples:  two BF16 planes; every int8 value is exact;
+//   * float samples: six BF16 planes of integer digits.  Per input and time
+//     window of W samples each component is quantised against the window's
+//     largest magnitude 2^E to a 23-bit integer M = d0 2^16 + d1 2^8 + d2
+//     with balanced digits |d_p| <= 128 (exact BF16 values); a product of two
+//     components is the sum of the digit products d_p d_q 2^(-8(p+q)) with
+//     p + q <= 2 (the dropped ones are below 2^-23 of the largest product).
+// The K axis runs over (time window, plane pair, stage): for 4-bit and int8
+// input a single pair (the re/im planes against themselves), for float input
+// the six digit pairs (p, q).  Each (window, pair) block is accumulated in
+// FP32 tensor memory and drained on its own: every partial sum of a block is
+// an integer of magnitude below 2^24 (at most 128, 32768 or 2 * 2^14 per
+// sample for 4-bit, int8 and digit products), so it is exact -- which matters
+// because the tensor core truncates each accumulation toward zero -- and the
+// drain converts it exactly to int32, or scales it by 2^(E_i + E_j - 12 -
+// 8(p + q)) and adds it (rounded to nearest) into a float accumulator.
+//
 // The input triangle is cut into 128 x 128 tile pairs (I >= J); a persistent
 // CTA walks a static list of (channel, I, J) items, channel-major, so the
-// CTAs in flight share the channels' planes in L2.  Per 64-sample stage, TMA
-// brings the four 64 x 128 E4M3 tiles Xr_I, Xi_I, Xr_J, Xi_J (two on the
-// diagonal) into a six-deep shared-memory ring as MN-major operands, and one thread issues,
-// per 32-sample step, three MMAs into an FP32 accumulator of 256 TMEM columns
-// holding [Re | -Im]:
+// CTAs in flight share the channels' planes in L2.  Per stage TMA brings the
+// four tiles Xr_p(I), Xi_p(I), Xr_q(J), Xi_q(J) (two when I == J and p == q)
+// into a shared-memory ring as MN-major operands (the transpose of the corner
+// turn happens in the operand fetch), and one thread issues, per MMA step,
+// three MMAs into an FP32 accumulator of 256 TMEM columns holding [Re | -Im]:
 //     [Re | -Im] += Xr_I [Xr_J | Xi_J]^T       (M = 128, N = 256)
 //     Re         += Xi_I Xi_J^T                (N = 128)
 //     -Im        += (-Xi_I) Xr_J^T             (N = 128, negate-A bit)
-// Every product is exact (4-bit integers are E4M3 values), and FP32 sums of
-// integers are exact below 2^24, so the K axis is cut into windows of at most
-// 130,944 samples (128 * 130,944 < 2^24); each window is drained to int32.  Two
-// accumulator buffers (512 columns) let the epilogue of one window overlap the
+// Two accumulator buffers (512 columns) let the drain of one block overlap the
 // MMAs of the next.
 //
 // Warp roles (192 threads, one CTA per SM): warps 0-3 drain TMEM (thread =
-// accumulator row) and add the lower-triangle part of the tile into the packed
-// int32 accumulator through a shared-memory transpose that makes the global
+// accumulator row) through a shared-memory transpose that makes the global
 // stores row-contiguous; warp 4 is the TMA producer; warp 5 allocates TMEM and
-// issues the MMAs.
+// issues the MMAs.  Every wait is bounded (see sm103_ptx.cuh).
 #include "sm103_ptx.cuh"
 #include "xcorr_internal.h"
 
 namespace xc {
 namespace {
 
-constexpr int kBlk = 128;                   // inputs per tile side
-constexpr int kKT = kTcStageT;              // samples per stage
-constexpr int kTileBytes = kBlk * kKT;      // one E4M3 plane tile: 8 KB
-constexpr int kStageBytes = 4 * kTileBytes; // Xr_I, Xi_I, Xr_J, Xi_J
-constexpr int kStages = 6;
+constexpr int kBlk = 128;          // inputs per tile side
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 192;
 constexpr int kProducerWarp = 4;
 constexpr int kMmaWarp = 5;
 constexpr int kChunk = 16;         // accumulator columns per epilogue step
-constexpr int kPitch = kChunk + 1; // int2 per staged row
+constexpr int kPitch = kChunk + 1; // 8-byte words per staged row
 constexpr int kAccCols = 256;      // [Re | -Im]
 constexpr uint32_t kTmemCols = 512;
 constexpr int kStagingBytes = kEpiWarps * 32 * kPitch * 8;
 constexpr int kBarrierBytes = 256;
-constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kStagingBytes + kBarrierBytes;
-static_assert(kSmemBytes <= 232448, "shared memory budget");
+
+// Stage shape of variant v: stage bytes 64 KB x 3, 48 KB x 4 or 32 KB x 6.
+constexpr int stage_rows_of(int v, int esize) { return (v == 0 ? 128 : v == 1 ? 96 : 64) / esize; }
+constexpr int stages_of(int v) { return v == 0 ? 3 : v == 1 ? 4 : 6; }
+
+template <int ESIZE, int KT, int STAGES>
+struct Geometry {
+  static constexpr int kChunksPerTile = kBlk * ESIZE / 128;  // 128-byte MN chunks
+  static constexpr int kChunkBytes = KT * 128;               // one chunk: KT rows of 128 B
+  static constexpr int kTileBytes = kChunksPerTile * kChunkBytes;
+  static constexpr int kStageBytes = 4 * kTileBytes;
+  static constexpr int kMmaK = 32 / ESIZE;                   // K of one MMA (rows)
+  static constexpr int kSteps = KT / kMmaK;
+  static constexpr int kSmemBytes = 1024 + STAGES * kStageBytes + kStagingBytes + kBarrierBytes;
+  static_assert(KT % kMmaK == 0, "stage must hold whole MMA steps");
+  static_assert(KT % 8 == 0, "swizzle atoms are 8 rows");
+  static_assert(kSmemBytes <= 232448, "shared memory budget");
+};
 
 struct TcParams {
-  int chan0, n_chan, n_inputs, n_tile_pairs, n_kblocks, kb_per_window;
+  int chan0, n_chan, n_inputs, n_tile_pairs;
+  int n_kt;           // stages along time
+  int n_pairs_k;      // plane pairs on the K axis
+  int spw;            // stages per time window
+  int n_tw;           // time windows
+  int planes_per_chan;
   int64_t n_pairs;
-  int accumulate_first;  // the first window adds into acc (else it stores)
-  int2* acc;
+  int accumulate_first;  // the first block adds into out (else it stores)
+  void* out;             // int2 or float2 [C][P]
   int* status;
+  const int8_t* exps;    // float input: window exponents [C][exp_windows][ni_pad]
+  int exp_windows, ni_pad;
+  int8_t pair_p[8], pair_q[8];  // digit indices of each plane pair
 };
 
 __device__ __forceinline__ void tile_pair(int p, int& I, int& J) {
@@ -67,15 +102,25 @@ __device__ __forceinline__ void tile_pair(int p, int& I, int& J) {
   J = p - i * (i + 1) / 2;
 }
 
+template <int ESIZE>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if (ESIZE == 1)
+    mma_f8f6f4(d, a, b, id, acc);
+  else
+    mma_f16(d, a, b, id, acc);
+}
+
+template <int ESIZE, int KT, int STAGES, bool FLOAT_OUT>
 __global__ void __launch_bounds__(kThreads, 1)
-    xcorr_tc_e4m3_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams p) {
+    xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TcParams p) {
+  using G = Geometry<ESIZE, KT, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stages = smem;
-  int2* staging = reinterpret_cast<int2*>(smem + kStages * kStageBytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes + kStagingBytes);
-  uint64_t* empty = full + kStages;
-  uint64_t* tfull = empty + kStages;
+  uint2* staging = reinterpret_cast<uint2*>(smem + STAGES * G::kStageBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * G::kStageBytes + kStagingBytes);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
   uint64_t* mma_done = tempty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_done + 1);
@@ -83,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -102,61 +147,75 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tslot;
 
   const int n_items = p.n_chan * p.n_tile_pairs;
-  const int n_windows = (p.n_kblocks + p.kb_per_window - 1) / p.kb_per_window;
+  const int n_blocks = p.n_tw * p.n_pairs_k;  // drained blocks per item: (window, pair)
 
   if (warp == kProducerWarp) {
     if (lane == 0) {
       prefetch_tmap(&tmap);
       int s = 0;
-      uint32_t ph = 0, filled = 0, fill_parity[kStages] = {};
+      uint32_t ph = 0, filled = 0, fill_parity[STAGES] = {};
       bool ok = true;
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
         const int cl = item / p.n_tile_pairs;
-        const int c = p.chan0 + cl;
+        const int zc = (p.chan0 + cl) * p.planes_per_chan;
+        const int half = p.planes_per_chan / 2;  // re planes, then im planes
         int I, J;
         tile_pair(item - cl * p.n_tile_pairs, I, J);
-        const bool diag = (I == J);
-        for (int kb = 0; kb < p.n_kblocks; ++kb) {
+        for (int blk = 0; ok && blk < n_blocks; ++blk) {
+          const int w = blk / p.n_pairs_k, pk = blk - w * p.n_pairs_k;
+          const int pp = p.pair_p[pk], pq = p.pair_q[pk];
+          const bool shared = (I == J) && (pp == pq);
+          const int tb1 = min(p.n_kt, (w + 1) * p.spw);
+        for (int tb = w * p.spw; tb < tb1; ++tb) {
+          const int t0 = tb * KT;
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
             ok = false;
             break;
           }
-          uint8_t* st = stages + s * kStageBytes;
-          mbar_expect_tx(&full[s], (diag ? 2 : 4) * kTileBytes);
-          tma_load_3d(st, &tmap, &full[s], I * kBlk, kb * kKT, 2 * c);
-          tma_load_3d(st + kTileBytes, &tmap, &full[s], I * kBlk, kb * kKT, 2 * c + 1);
-          if (!diag) {
-            tma_load_3d(st + 2 * kTileBytes, &tmap, &full[s], J * kBlk, kb * kKT, 2 * c);
-            tma_load_3d(st + 3 * kTileBytes, &tmap, &full[s], J * kBlk, kb * kKT, 2 * c + 1);
+          uint8_t* st = stages + s * G::kStageBytes;
+          mbar_expect_tx(&full[s], (shared ? 2 : 4) * G::kTileBytes);
+#pragma unroll
+          for (int ch = 0; ch < G::kChunksPerTile; ++ch) {
+            const int xi = I * kBlk + ch * (128 / ESIZE), xj = J * kBlk + ch * (128 / ESIZE);
+            tma_load_3d(st + ch * G::kChunkBytes, &tmap, &full[s], xi, t0, zc + pp);
+            tma_load_3d(st + G::kTileBytes + ch * G::kChunkBytes, &tmap, &full[s], xi, t0, zc + half + pp);
+            if (!shared) {
+              tma_load_3d(st + 2 * G::kTileBytes + ch * G::kChunkBytes, &tmap, &full[s], xj, t0, zc + pq);
+              tma_load_3d(st + 3 * G::kTileBytes + ch * G::kChunkBytes, &tmap, &full[s], xj, t0, zc + half + pq);
+            }
           }
           fill_parity[s] = ph;
           filled |= 1u << s;
-          if (++s == kStages) {
+          if (++s == STAGES) {
             s = 0;
             ph ^= 1u;
           }
         }
+        }
       }
       // Let every copy this CTA issued land before the CTA can exit.
       volatile int never = 0;
-      for (int q = 0; q < kStages; ++q)
+      for (int q = 0; q < STAGES; ++q)
         if (filled & (1u << q)) mbar_wait(&full[q], fill_parity[q], &never, p.status, DEV_TIMEOUT_DRAIN);
     }
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
-      const uint32_t id256 = instr_desc(kTypeE4M3, true, 128, 256, false);
-      const uint32_t id128 = instr_desc(kTypeE4M3, true, 128, 128, false);
-      const uint32_t id128n = instr_desc(kTypeE4M3, true, 128, 128, true);
+      const uint32_t type = ESIZE == 1 ? kTypeE4M3 : kTypeBF16;
+      const uint32_t id256 = instr_desc(type, true, 128, 256, false);
+      const uint32_t id128 = instr_desc(type, true, 128, 128, false);
+      const uint32_t id128n = instr_desc(type, true, 128, 128, true);
+      constexpr uint32_t kLbo = G::kChunkBytes;  // distance between 128-byte M/N chunks
       int s = 0;
       uint32_t ph = 0;
       int g = 0;  // windows processed by this CTA
       bool ok = true;
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-        const int c = item / p.n_tile_pairs;
+        const int cl = item / p.n_tile_pairs;
         int I, J;
-        tile_pair(item - c * p.n_tile_pairs, I, J);
-        const bool diag = (I == J);
-        for (int w = 0; ok && w < n_windows; ++w, ++g) {
+        tile_pair(item - cl * p.n_tile_pairs, I, J);
+        for (int blk = 0; ok && blk < n_blocks; ++blk, ++g) {
+          const int w = blk / p.n_pairs_k, pk = blk - w * p.n_pairs_k;
+          const bool shared = (I == J) && (p.pair_p[pk] == p.pair_q[pk]);
           const int buf = g & 1;
           const uint32_t use = static_cast<uint32_t>(g >> 1);
           if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_EMPTY)) {
@@ -165,31 +224,31 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem + static_cast<uint32_t>(buf * kAccCols);
-          const int kb0 = w * p.kb_per_window;
-          const int kb1 = min(p.n_kblocks, kb0 + p.kb_per_window);
+          const int kb0 = w * p.spw;
+          const int kb1 = min(p.n_kt, kb0 + p.spw);
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&full[s], ph, abort_flag, p.status, DEV_TIMEOUT_FULL)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t a_r = smem_u32(stages + s * kStageBytes);
-            const uint32_t a_i = a_r + kTileBytes;
-            const uint32_t b_r = diag ? a_r : a_r + 2 * kTileBytes;
-            const uint32_t b_i = b_r + kTileBytes;
+            const uint32_t a_r = smem_u32(stages + s * G::kStageBytes);
+            const uint32_t a_i = a_r + G::kTileBytes;
+            const uint32_t b_r = shared ? a_r : a_r + 2 * G::kTileBytes;
+            const uint32_t b_i = b_r + G::kTileBytes;
 #pragma unroll
-            for (int k = 0; k < kKT / 32; ++k) {
-              const uint32_t off = static_cast<uint32_t>(k) * 32u * kBlk;  // 32 rows of 128 B
+            for (int k = 0; k < G::kSteps; ++k) {
+              const uint32_t off = static_cast<uint32_t>(k * G::kMmaK * 128);  // kMmaK rows of 128 B
               const uint32_t first = (kb == kb0 && k == 0) ? 1u : 0u;
-              mma_f8f6f4(d, smem_desc_sw128(a_r + off, kTileBytes, 1024),
-                         smem_desc_sw128(b_r + off, kTileBytes, 1024), id256, first ^ 1u);
-              mma_f8f6f4(d, smem_desc_sw128(a_i + off, kTileBytes, 1024),
-                         smem_desc_sw128(b_i + off, kTileBytes, 1024), id128, 1u);
-              mma_f8f6f4(d + 128, smem_desc_sw128(a_i + off, kTileBytes, 1024),
-                         smem_desc_sw128(b_r + off, kTileBytes, 1024), id128n, 1u);
+              mma<ESIZE>(d, smem_desc_sw128(a_r + off, kLbo, 1024), smem_desc_sw128(b_r + off, kLbo, 1024),
+                         id256, first ^ 1u);
+              mma<ESIZE>(d, smem_desc_sw128(a_i + off, kLbo, 1024), smem_desc_sw128(b_i + off, kLbo, 1024),
+                         id128, 1u);
+              mma<ESIZE>(d + 128, smem_desc_sw128(a_i + off, kLbo, 1024),
+                         smem_desc_sw128(b_r + off, kLbo, 1024), id128n, 1u);
             }
             mma_commit(&empty[s]);
-            if (++s == kStages) {
+            if (++s == STAGES) {
               s = 0;
               ph ^= 1u;
             }
@@ -204,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // Epilogue: warp w drains TMEM lanes 32w .. 32w + 31 (tile rows).
-    int2* stage_rows = staging + warp * 32 * kPitch;
+    uint2* stage_rows = staging + warp * 32 * kPitch;
     const int half = lane >> 4, col = lane & 15;
     int g = 0;
     bool ok = true;
@@ -212,9 +271,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int cl = item / p.n_tile_pairs;
       int I, J;
       tile_pair(item - cl * p.n_tile_pairs, I, J);
-      int2* acc_c = p.acc + (int64_t)(p.chan0 + cl) * p.n_pairs;
+      uint2* out_c = static_cast<uint2*>(p.out) + (int64_t)(p.chan0 + cl) * p.n_pairs;
       const int row0 = I * kBlk + warp * 32;  // first global input row of this warp
-      for (int w = 0; w < n_windows; ++w, ++g) {
+      for (int blk = 0; blk < n_blocks; ++blk, ++g) {
         const int buf = g & 1;
         const uint32_t use = static_cast<uint32_t>(g >> 1);
         if (!mbar_wait(&tfull[buf], use & 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL)) {
@@ -222,7 +281,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const bool add = (w > 0) || p.accumulate_first;
+        const bool add = (blk > 0) || p.accumulate_first;
+        // float input: this block's scale 2^(E_i + E_j - 12 - 8(p + q)), split
+        // into the row factor (E_i) and the column factors (E_j, per chunk)
+        const int8_t* exps_w = nullptr;
+        float row_scale = 1.f;
+        if (FLOAT_OUT) {
+          const int w = blk / p.n_pairs_k, pk = blk - w * p.n_pairs_k;
+          exps_w = p.exps + ((int64_t)(p.chan0 + cl) * p.exp_windows + w) * p.ni_pad;
+          const int i_row = min(row0 + lane, p.n_inputs - 1);
+          row_scale = ldexpf(1.f, static_cast<int>(exps_w[i_row]) - 12 - 8 * (p.pair_p[pk] + p.pair_q[pk]));
+        }
         const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + buf * kAccCols;
         for (int j0 = 0; j0 < kBlk; j0 += kChunk) {
           uint32_t re[16], nim[16];
@@ -234,9 +303,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           const bool any = (jfirst <= row0 + 31) && (row0 < p.n_inputs);
           if (any) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
-              stage_rows[lane * kPitch + q] = make_int2(__float2int_rn(__uint_as_float(re[q])),
-                                                        -__float2int_rn(__uint_as_float(nim[q])));
+            for (int q = 0; q < 16; ++q) {
+              if (FLOAT_OUT) {
+                // exact integer block sums times an exact power of two
+                const int jq = min(jfirst + q, p.n_inputs - 1);
+                const float sc = ldexpf(row_scale, static_cast<int>(exps_w[jq]));
+                stage_rows[lane * kPitch + q] = make_uint2(__float_as_uint(__uint_as_float(re[q]) * sc),
+                                                           __float_as_uint(-__uint_as_float(nim[q]) * sc));
+              } else {
+                stage_rows[lane * kPitch + q] =
+                    make_uint2(static_cast<uint32_t>(__float2int_rn(__uint_as_float(re[q]))),
+                               static_cast<uint32_t>(-__float2int_rn(__uint_as_float(nim[q]))));
+              }
+            }
             __syncwarp();
 #pragma unroll 4
             for (int r = 0; r < 32; r += 2) {
@@ -244,12 +323,17 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int i = row0 + rr;
               const int j = jfirst + col;
               if (i < p.n_inputs && j <= i) {
-                int2 v = stage_rows[rr * kPitch + col];
-                int2* dst = acc_c + (int64_t)i * (i + 1) / 2 + j;
+                uint2 v = stage_rows[rr * kPitch + col];
+                uint2* dst = out_c + (int64_t)i * (i + 1) / 2 + j;
                 if (add) {
-                  const int2 o = *dst;
-                  v.x += o.x;
-                  v.y += o.y;
+                  const uint2 o = *dst;
+                  if (FLOAT_OUT) {
+                    v.x = __float_as_uint(__uint_as_float(v.x) + __uint_as_float(o.x));
+                    v.y = __float_as_uint(__uint_as_float(v.y) + __uint_as_float(o.y));
+                  } else {
+                    v.x += o.x;
+                    v.y += o.y;
+                  }
                 }
                 *dst = v;
               }
@@ -272,34 +356,75 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// One instantiation per (operand type, stage variant, output type) in use.
+template <int ESIZE, int V, bool FLOAT_OUT>
+cudaError_t launch_variant(const CUtensorMap* tmap, const TcParams& p, int grid, cudaStream_t stream) {
+  constexpr int KT = stage_rows_of(V, ESIZE), S = stages_of(V);
+  using G = Geometry<ESIZE, KT, S>;
+  auto kern = xcorr_tc_kernel<ESIZE, KT, S, FLOAT_OUT>;
+  static int attr_device = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (attr_device != dev) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_device = dev;
+  }
+  kern<<<grid, kThreads, G::kSmemBytes, stream>>>(*tmap, p);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_xcorr_tc_e4m3(const CUtensorMap* tmap, int n_time, int chan0, int n_chan,
-                                 int n_inputs, int2* acc, bool accumulate, int* status,
-                                 int num_sms, cudaStream_t stream) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(xcorr_tc_e4m3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  const int nb = (n_inputs + kBlk - 1) / kBlk;
-  TcParams p;
-  p.chan0 = chan0;
-  p.n_chan = n_chan;
-  p.n_inputs = n_inputs;
+int tc_stage_samples(int elem_bytes, int variant) { return stage_rows_of(variant, elem_bytes); }
+
+cudaError_t launch_xcorr_tc(const CUtensorMap* tmap, const TcLaunch& L, cudaStream_t stream) {
+  const int nb = (L.n_inputs + kBlk - 1) / kBlk;
+  const int kt = stage_rows_of(L.variant, L.elem_bytes);
+  TcParams p{};
+  p.chan0 = L.chan0;
+  p.n_chan = L.n_chan;
+  p.n_inputs = L.n_inputs;
   p.n_tile_pairs = nb * (nb + 1) / 2;
-  p.n_kblocks = (n_time + kKT - 1) / kKT;
-  p.kb_per_window = kTcMaxKblocksPerWindow;
-  p.n_pairs = (int64_t)n_inputs * (n_inputs + 1) / 2;
-  p.accumulate_first = accumulate ? 1 : 0;
-  p.acc = acc;
-  p.status = status;
-  const int64_t items = (int64_t)n_chan * p.n_tile_pairs;
-  const int grid = static_cast<int>(items < num_sms ? items : num_sms);
-  xcorr_tc_e4m3_kernel<<<grid, kThreads, kSmemBytes, stream>>>(*tmap, p);
-  return cudaGetLastError();
+  p.n_kt = (L.n_time + kt - 1) / kt;
+  p.n_pairs_k = L.n_pairs_k;
+  p.spw = L.window_samples / kt;
+  p.n_tw = (p.n_kt + p.spw - 1) / p.spw;
+  p.planes_per_chan = L.planes_per_chan;
+  p.exps = L.exps;
+  p.exp_windows = L.exp_windows;
+  p.ni_pad = L.ni_pad;
+  p.n_pairs = (int64_t)L.n_inputs * (L.n_inputs + 1) / 2;
+  p.accumulate_first = L.accumulate ? 1 : 0;
+  p.out = L.out;
+  p.status = L.status;
+  for (int k = 0; k < 8; ++k) {
+    p.pair_p[k] = static_cast<int8_t>(k < L.n_pairs_k ? L.pair_p[k] : 0);
+    p.pair_q[k] = static_cast<int8_t>(k < L.n_pairs_k ? L.pair_q[k] : 0);
+  }
+  if (p.spw < 1 || L.window_samples % kt || (L.float_out && !L.exps)) return cudaErrorInvalidValue;
+  const int64_t items = (int64_t)L.n_chan * p.n_tile_pairs;
+  const int grid = static_cast<int>(items < L.num_sms ? items : L.num_sms);
+  if (L.elem_bytes == 1) {
+    switch (L.variant) {
+      case 0: return launch_variant<1, 0, false>(tmap, p, grid, stream);
+      case 1: return launch_variant<1, 1, false>(tmap, p, grid, stream);
+      default: return launch_variant<1, 2, false>(tmap, p, grid, stream);
+    }
+  }
+  if (L.float_out) {
+    switch (L.variant) {
+      case 0: return launch_variant<2, 0, true>(tmap, p, grid, stream);
+      case 1: return launch_variant<2, 1, true>(tmap, p, grid, stream);
+      default: return launch_variant<2, 2, true>(tmap, p, grid, stream);
+    }
+  }
+  switch (L.variant) {
+    case 0: return launch_variant<2, 0, false>(tmap, p, grid, stream);
+    case 1: return launch_variant<2, 1, false>(tmap, p, grid, stream);
+    default: return launch_variant<2, 2, false>(tmap, p, grid, stream);
+  }
 }
 
 }  // namespace xc

@@ -9,6 +9,7 @@
 // the X kernel reads them as MN-major operands, so the tensor memory access
 // itself performs the transpose of the corner turn and this kernel is a pure
 // element-wise decode with 128-bit loads and stores.
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <cstring>
@@ -133,25 +134,178 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled_fn(std::string* err) {
 }
 }  // namespace
 
-bool encode_plane_tmap(CUtensorMap* map, void* planes, int n_inputs, int ni_pad, int n_time,
-                       int max_time, int n_chan, std::string* err) {
+bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inputs, int ni_pad,
+                       int n_time, int max_time, int n_planes_total, int box_t, std::string* err) {
   auto fn = encode_tiled_fn(err);
   if (!fn) return false;
   std::memset(map, 0, sizeof(*map));
-  // dim0: input (contiguous), dim1: time, dim2: channel * 2 + component.  Rows
+  // dim0: input (contiguous), dim1: time, dim2: channel * planes + plane.  Inputs
   // past n_inputs and times past n_time read as zeros.
-  cuuint64_t dims[3] = {(cuuint64_t)n_inputs, (cuuint64_t)n_time, (cuuint64_t)n_chan * 2};
-  cuuint64_t strides[2] = {(cuuint64_t)ni_pad, (cuuint64_t)ni_pad * (cuuint64_t)max_time};
-  cuuint32_t box[3] = {128, (cuuint32_t)kTcStageT, 1};
+  const cuuint64_t row = (cuuint64_t)ni_pad * elem_bytes;
+  cuuint64_t dims[3] = {(cuuint64_t)n_inputs, (cuuint64_t)n_time, (cuuint64_t)n_planes_total};
+  cuuint64_t strides[2] = {row, row * (cuuint64_t)max_time};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_t, 1};
   cuuint32_t elem_strides[3] = {1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, planes, dims, strides, box, elem_strides,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  CUresult r = fn(map, elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, planes,
+                  dims, strides, box, elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     if (err) *err = "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r);
     return false;
   }
   return true;
+}
+
+// ----------------------------------------------------- int8 and float input --
+namespace {
+
+__device__ __forceinline__ uint32_t bf16_bits(float f) {
+  return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(f)));
+}
+
+// Eight int8 samples (16 bytes: re, im interleaved) -> eight BF16 real parts
+// and eight imaginary parts, exact (|v| <= 128 needs 8 significant bits).
+__global__ void __launch_bounds__(256) unpack_ci8_bf16_vec(const int8_t* __restrict__ in,
+                                                           uint16_t* __restrict__ planes, int64_t n_rows,
+                                                           int n_chan, int c0, int nc, int q_per_row,
+                                                           int ni_pad, int64_t comp_stride) {
+  const int64_t total = n_rows * q_per_row;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = q / q_per_row;
+    const int k = static_cast<int>(q - row * q_per_row);
+    const int64_t t = row / nc;
+    const int c = c0 + static_cast<int>(row - t * nc);
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + ((t * n_chan + c) * q_per_row + k) * 16));
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t re[4], im[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {  // word h holds samples 2h, 2h + 1: re0 im0 re1 im1
+      const float r0 = static_cast<float>(static_cast<int8_t>(w[h] & 0xFF));
+      const float i0 = static_cast<float>(static_cast<int8_t>((w[h] >> 8) & 0xFF));
+      const float r1 = static_cast<float>(static_cast<int8_t>((w[h] >> 16) & 0xFF));
+      const float i1 = static_cast<float>(static_cast<int8_t>(w[h] >> 24));
+      re[h] = bf16_bits(r0) | (bf16_bits(r1) << 16);
+      im[h] = bf16_bits(i0) | (bf16_bits(i1) << 16);
+    }
+    uint16_t* dst = planes + (2 * (int64_t)c) * comp_stride + t * ni_pad + 8 * (int64_t)k;
+    *reinterpret_cast<uint4*>(dst) = make_uint4(re[0], re[1], re[2], re[3]);
+    *reinterpret_cast<uint4*>(dst + comp_stride) = make_uint4(im[0], im[1], im[2], im[3]);
+  }
+}
+
+__global__ void __launch_bounds__(256) unpack_ci8_bf16_elem(const int8_t* __restrict__ in,
+                                                            uint16_t* __restrict__ planes, int64_t n_rows,
+                                                            int n_chan, int c0, int nc, int n_inputs,
+                                                            int ni_pad, int64_t comp_stride) {
+  const int64_t total = n_rows * n_inputs;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = q / n_inputs;
+    const int i = static_cast<int>(q - row * n_inputs);
+    const int64_t t = row / nc;
+    const int c = c0 + static_cast<int>(row - t * nc);
+    const int64_t s = (t * n_chan + c) * n_inputs + i;
+    uint16_t* dst = planes + (2 * (int64_t)c) * comp_stride + t * ni_pad + i;
+    dst[0] = static_cast<uint16_t>(bf16_bits(static_cast<float>(in[2 * s])));
+    dst[comp_stride] = static_cast<uint16_t>(bf16_bits(static_cast<float>(in[2 * s + 1])));
+  }
+}
+
+// Float input, one thread per (channel, window, input): find the window's
+// largest magnitude max < 2^(E+1), quantise each component to the integer
+// M = rint(x 2^(22-E)) (|M| < 2^23, error <= 2^-23 max), and write the
+// balanced base-256 digits of M = d0 2^16 + d1 2^8 + d2 (|d_p| <= 128, exact
+// BF16 values) to planes re_p = p and im_p = 3 + p.  E goes to exps.
+__device__ __forceinline__ void digits_of(float x, float scale, uint16_t (&d)[3]) {
+  const int m = __float2int_rn(x * scale);
+  const int d2 = ((m + 128) & 255) - 128;
+  const int m1 = (m - d2) >> 8;
+  const int d1 = ((m1 + 128) & 255) - 128;
+  const int d0 = (m1 - d1) >> 8;
+  d[0] = __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d0)));
+  d[1] = __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d1)));
+  d[2] = __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d2)));
+}
+
+__global__ void __launch_bounds__(256) unpack_cf32_digits_kernel(const float2* __restrict__ in,
+                                                                 uint16_t* __restrict__ planes,
+                                                                 int8_t* __restrict__ exps, int n_time, int n_chan,
+                                                                 int c0, int nc, int n_inputs, int ni_pad,
+                                                                 int64_t comp_stride, int window, int exp_windows) {
+  const int n_w = (n_time + window - 1) / window;
+  const int64_t total = (int64_t)nc * n_w * n_inputs;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int i = static_cast<int>(q % n_inputs);
+    const int64_t rest = q / n_inputs;
+    const int w = static_cast<int>(rest % n_w);
+    const int c = c0 + static_cast<int>(rest / n_w);
+    const int t0 = w * window, t1 = min(n_time, t0 + window);
+    float mx = 0.f;
+    for (int t = t0; t < t1; ++t) {
+      const float2 v = __ldg(in + ((int64_t)t * n_chan + c) * n_inputs + i);
+      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    int e = 0;
+    if (mx > 0.f) {
+      frexpf(mx, &e);  // mx = f 2^e with f in [0.5, 1): mx < 2^e
+      e -= 1;
+    }
+    e = max(e, -64);
+    exps[((int64_t)c * exp_windows + w) * ni_pad + i] = static_cast<int8_t>(e);
+    const float scale = ldexpf(1.f, 22 - e);
+    uint16_t* base = planes + (6 * (int64_t)c) * comp_stride + i;
+    for (int t = t0; t < t1; ++t) {
+      const float2 v = __ldg(in + ((int64_t)t * n_chan + c) * n_inputs + i);
+      uint16_t dr[3], dm[3];
+      digits_of(v.x, scale, dr);
+      digits_of(v.y, scale, dm);
+      uint16_t* row = base + (int64_t)t * ni_pad;
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc) {
+        row[pc * comp_stride] = dr[pc];
+        row[(3 + pc) * comp_stride] = dm[pc];
+      }
+    }
+  }
+}
+
+int64_t grid_for(int64_t work, int num_sms) {
+  int64_t blocks = (work + 255) / 256;
+  const int64_t cap = (int64_t)num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  return blocks < 1 ? 1 : blocks;
+}
+
+}  // namespace
+
+cudaError_t launch_unpack_ci8_bf16(const int8_t* in, uint16_t* planes, int n_time, int n_chan, int c0, int nc,
+                                   int n_inputs, int ni_pad, int max_time, int num_sms, cudaStream_t stream) {
+  const int64_t n_rows = (int64_t)n_time * nc;
+  const int64_t comp_stride = (int64_t)max_time * ni_pad;
+  const bool vec = (n_inputs % 8 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0);
+  if (vec)
+    unpack_ci8_bf16_vec<<<(unsigned)grid_for(n_rows * (n_inputs / 8), num_sms), 256, 0, stream>>>(
+        in, planes, n_rows, n_chan, c0, nc, n_inputs / 8, ni_pad, comp_stride);
+  else
+    unpack_ci8_bf16_elem<<<(unsigned)grid_for(n_rows * n_inputs, num_sms), 256, 0, stream>>>(
+        in, planes, n_rows, n_chan, c0, nc, n_inputs, ni_pad, comp_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_cf32_digits(const float* in, uint16_t* planes, int8_t* exps, int n_time, int n_chan,
+                                      int c0, int nc, int n_inputs, int ni_pad, int max_time, int window,
+                                      int exp_windows, cudaStream_t stream) {
+  const int64_t comp_stride = (int64_t)max_time * ni_pad;
+  const int64_t work = (int64_t)nc * ((n_time + window - 1) / window) * n_inputs;
+  int64_t blocks = (work + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > (1 << 20)) blocks = 1 << 20;
+  unpack_cf32_digits_kernel<<<(unsigned)blocks, 256, 0, stream>>>(reinterpret_cast<const float2*>(in), planes, exps,
+                                                                  n_time, n_chan, c0, nc, n_inputs, ni_pad,
+                                                                  comp_stride, window, exp_windows);
+  return cudaGetLastError();
 }
 
 }  // namespace xc

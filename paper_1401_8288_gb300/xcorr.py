@@ -30,7 +30,7 @@ ENGINES = {"auto": XCORR_ENGINE_AUTO, "tensor": XCORR_ENGINE_TENSOR,
 EXPORTS = ("xcorr_plan_create", "xcorr_execute", "xcorr_dump", "xcorr_sync", "xcorr_plan_query",
            "xcorr_destroy", "xcorr_last_error", "xcorr_baseline_index", "xcorr_profile_enable",
            "xcorr_profile_read", "xcorr_measure_peak", "xcorr_correlate_ci4_noalloc",
-           "xcorr_execute_dump")
+           "xcorr_execute_dump", "xcorr_plan_set_tuning", "xcorr_autotune")
 PEAK_KINDS = {"tc_e4m3": 0, "tc_bf16": 1, "mma_sync_s8": 2, "dp4a": 3}
 
 
@@ -47,12 +47,17 @@ class xcorr_config(ctypes.Structure):
                 ("hbm_budget_bytes", ctypes.c_size_t)]
 
 
+class xcorr_tuning(ctypes.Structure):
+    _fields_ = [("stage_variant", ctypes.c_int), ("groups", ctypes.c_int),
+                ("x_streams", ctypes.c_int)]
+
+
 class xcorr_plan_info(ctypes.Structure):
     _fields_ = [("n_inputs", ctypes.c_int), ("n_channels", ctypes.c_int),
                 ("n_pairs", ctypes.c_int64), ("engine", ctypes.c_int),
                 ("samples_integrated", ctypes.c_int64), ("max_integration", ctypes.c_int64),
                 ("device_bytes", ctypes.c_size_t), ("output_bytes", ctypes.c_size_t),
-                ("kernels_per_execute", ctypes.c_int)]
+                ("kernels_per_execute", ctypes.c_int), ("tuning", xcorr_tuning)]
 
 
 _lib = None
@@ -86,6 +91,9 @@ def load():
                 "xcorr_profile_read": [vp, ctypes.POINTER(ctypes.c_float), i, ctypes.POINTER(i)],
                 "xcorr_measure_peak": [i, ctypes.POINTER(ctypes.c_double)],
                 "xcorr_correlate_ci4_noalloc": [vp, i, i, i, vp, vp, vp],
+                "xcorr_plan_set_tuning": [vp, ctypes.POINTER(xcorr_tuning)],
+                "xcorr_autotune": [vp, vp, i, vp, ctypes.POINTER(xcorr_tuning),
+                                   ctypes.POINTER(ctypes.c_float)],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -138,10 +146,28 @@ def xcorr_sync(plan, stream: int = 0) -> None:
     _check(load().xcorr_sync(plan, stream))
 
 
+def _tuning_dict(t: xcorr_tuning) -> dict:
+    return {name: getattr(t, name) for name, _ in xcorr_tuning._fields_}
+
+
 def xcorr_plan_query(plan) -> dict:
     info = xcorr_plan_info()
     _check(load().xcorr_plan_query(plan, ctypes.byref(info)))
-    return {name: getattr(info, name) for name, _ in xcorr_plan_info._fields_}
+    out = {name: getattr(info, name) for name, _ in xcorr_plan_info._fields_}
+    out["tuning"] = _tuning_dict(info.tuning)
+    return out
+
+
+def xcorr_plan_set_tuning(plan, stage_variant: int = 0, groups: int = 0, x_streams: int = 2) -> None:
+    t = xcorr_tuning(stage_variant, groups, x_streams)
+    _check(load().xcorr_plan_set_tuning(plan, ctypes.byref(t)))
+
+
+def xcorr_autotune(plan, d_in: int, n_time: int, stream: int = 0) -> tuple[dict, float]:
+    """Time every launch shape on this input; the fastest is kept on the plan."""
+    t, ms = xcorr_tuning(), ctypes.c_float()
+    _check(load().xcorr_autotune(plan, d_in, n_time, stream, ctypes.byref(t), ctypes.byref(ms)))
+    return _tuning_dict(t), ms.value
 
 
 def xcorr_destroy(plan) -> None:
@@ -190,9 +216,10 @@ class Plan:
     """A plan with PyTorch tensors for device memory and streams.
 
     ``execute(x)`` takes a CUDA tensor in the plan's input layout
-    (uint8 [t][c][s][2] for CI4, int8 [t][c][s][2][2] for CI8);
-    ``dump()`` returns the packed-triangle visibilities as an int32 tensor
-    [C][P][2] (or writes them into ``out``).
+    (uint8 [t][c][s][2] for CI4, int8 [t][c][s][2][2] for CI8, float32
+    [t][c][s][2][2] for CF32); ``dump()`` returns the packed-triangle
+    visibilities as a [C][P][2] tensor, int32 (float32 for CF32; int64 /
+    float64 with ``wide=True``), or writes them into ``out``.
     """
 
     def __init__(self, n_stations: int, n_channels: int, max_time_per_exec: int,
@@ -205,6 +232,18 @@ class Plan:
         self.info = xcorr_plan_query(self.handle)
         self.n_stations = n_stations
         self.n_channels = n_channels
+
+    def _out_dtype(self, wide: bool):
+        torch = self._torch
+        if self.fmt == "cf32":
+            return torch.float64 if wide else torch.float32
+        return torch.int64 if wide else torch.int32
+
+    def set_tuning(self, stage_variant: int = 0, groups: int = 0, x_streams: int = 2) -> None:
+        xcorr_plan_set_tuning(self.handle, stage_variant, groups, x_streams)
+
+    def autotune(self, x, stream=None) -> tuple[dict, float]:
+        return xcorr_autotune(self.handle, x.data_ptr(), x.shape[0], self._stream(stream))
 
     def _stream(self, stream) -> int:
         if stream is None:
@@ -221,7 +260,7 @@ class Plan:
         torch = self._torch
         shape = (self.n_channels, self.info["n_pairs"], 2)
         if out is None:
-            out = torch.zeros(shape, dtype=torch.int64 if wide else torch.int32, device="cuda")
+            out = torch.zeros(shape, dtype=self._out_dtype(wide), device="cuda")
         flags = (XCORR_DUMP_RESET if reset else 0) | (XCORR_DUMP_ADD_WIDE if wide else 0)
         self.samples = xcorr_dump(self.handle, out.data_ptr(), out.is_cuda, flags,
                                   self._stream(stream))
@@ -234,7 +273,7 @@ class Plan:
             raise ValueError("input must be a contiguous CUDA tensor")
         if out is None:
             out = torch.zeros((self.n_channels, self.info["n_pairs"], 2),
-                              dtype=torch.int64 if wide else torch.int32, device="cuda")
+                              dtype=self._out_dtype(wide), device="cuda")
         flags = (XCORR_DUMP_RESET if reset else 0) | (XCORR_DUMP_ADD_WIDE if wide else 0)
         self.samples = xcorr_execute_dump(self.handle, x.data_ptr(), x.shape[0], out.data_ptr(),
                                           out.is_cuda, flags, self._stream(stream))

@@ -55,8 +55,9 @@ def test_config_struct_layout_matches_c():
     (dict(n_stations=4, n_channels=4, max_time_per_exec=16, n_pols=1), 1),
     (dict(n_stations=4, n_channels=4, max_time_per_exec=16, fmt=7), 1),
     (dict(n_stations=4, n_channels=4, max_time_per_exec=16, engine=9), 1),
-    (dict(n_stations=4, n_channels=4, max_time_per_exec=16, fmt=xcorr.XCORR_IN_CI8,
-          engine=xcorr.XCORR_ENGINE_TENSOR), 2),
+    (dict(n_stations=4, n_channels=4, max_time_per_exec=16, fmt=xcorr.XCORR_IN_CF32,
+          engine=xcorr.XCORR_ENGINE_CUDA_CORE), 2),
+    (dict(n_stations=4, n_channels=4, max_time_per_exec=16777217, fmt=xcorr.XCORR_IN_CF32), 4),
     (dict(n_stations=4, n_channels=4, max_time_per_exec=70000, fmt=xcorr.XCORR_IN_CI8), 4),
     (dict(n_stations=4, n_channels=4, max_time_per_exec=16777216), 4),
 ])

@@ -26,13 +26,15 @@ def torch():
     return torch
 
 
-def run(torch, x, engine, fmt="ci4", n_time=None, chunks=None):
+def run(torch, x, engine, fmt="ci4", n_time=None, chunks=None, tuning=None):
     """Correlate x (host array) with one plan; optionally in several executes."""
     n_time = x.shape[0] if n_time is None else n_time
     n_sta, n_chan = x.shape[2], x.shape[1]
     xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     max_t = n_time if chunks is None else max(chunks)
     with xcorr.Plan(n_sta, n_chan, max_t, fmt=fmt, engine=engine) as plan:
+        if tuning is not None:
+            plan.set_tuning(*tuning)
         if chunks is None:
             plan.execute(xd)
         else:
@@ -42,7 +44,8 @@ def run(torch, x, engine, fmt="ci4", n_time=None, chunks=None):
                 t0 += k
         out = plan.dump()
         plan.sync()
-        return out.cpu().numpy().astype(np.int64), plan.samples
+        got = out.cpu().numpy()
+        return (got if fmt == "cf32" else got.astype(np.int64)), plan.samples
 
 
 @pytest.mark.parametrize("engine", ENGINES)
@@ -235,6 +238,107 @@ def test_budget_and_query(torch):
         assert info["engine"] == xcorr.XCORR_ENGINE_TENSOR
         assert info["max_integration"] == 16777215
         assert info["output_bytes"] == 64 * 131328 * 8
+
+
+# -------------------------------------------------- int8 on tensor cores ---
+
+@pytest.mark.parametrize("n_sta,n_chan,n_time", [(1, 2, 7), (37, 3, 150), (70, 2, 1000), (136, 2, 385)])
+def test_ci8_tensor_bit_exact(torch, n_sta, n_chan, n_time):
+    # full code range with -128; K beyond one 384-sample window drains int32 sums
+    x = synth.uniform_ci8(n_time, n_chan, n_sta, seed=n_sta + n_time)
+    got, _ = run(torch, x, "tensor", fmt="ci8")
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI8, x))
+
+
+def test_ci8_tensor_extreme_codes_at_the_int32_bound(torch):
+    k = 65535
+    x = np.full((k, 1, 4, 2, 2), -128, dtype=np.int8)
+    got, _ = run(torch, x, "tensor", fmt="ci8")
+    assert np.all(got[..., 0] == 32768 * k) and np.all(got[..., 1] == 0)
+
+
+def test_ci8_tensor_gaussian_sigma20(torch):
+    x = synth.gaussian_ci8(512, 4, 128, seed=14018288 + 3)
+    got, _ = run(torch, x, "tensor", fmt="ci8")
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI8, x))
+
+
+# --------------------------------------------------------- float input ---
+
+def normalised_error(got, want, n_inputs):
+    """|V - V_fp64| / sqrt(V_ii V_jj): the error scaled by the Cauchy-Schwarz
+    bound of each entry (a raw relative error is unbounded for cross terms
+    that happen to sum to about zero)."""
+    idx = np.arange(n_inputs)
+    autos = want[:, idx * (idx + 1) // 2 + idx, 0]  # [C][N]
+    ii, jj = np.tril_indices(n_inputs)
+    order = np.argsort(ii * (ii + 1) // 2 + jj)
+    scale = np.sqrt(autos[:, ii[order]] * autos[:, jj[order]])
+    err = np.abs((got[..., 0] - want[..., 0]) + 1j * (got[..., 1] - want[..., 1]))
+    return err / scale, np.abs(got[:, idx * (idx + 1) // 2 + idx, 0] / autos - 1)
+
+
+@pytest.mark.parametrize("n_sta,n_chan,n_time", [(1, 1, 3), (37, 2, 129), (70, 3, 700), (256, 2, 4096)])
+def test_cf32_tensor_within_1e6_of_fp64(torch, n_sta, n_chan, n_time):
+    x = synth.gaussian_cf32(n_time, n_chan, n_sta, seed=n_sta * 7 + n_time)
+    got, _ = run(torch, x, "tensor", fmt="cf32")
+    want = oracle.correlate(oracle.FMT_CF32, x)
+    e, e_auto = normalised_error(got.astype(np.float64), want, 2 * n_sta)
+    assert e.max() <= 1e-6, e.max()
+    assert e_auto.max() <= 1e-6, e_auto.max()
+
+
+def test_cf32_integer_valued_is_exact(torch):
+    # integer-valued floats have exact pieces and exact short sums
+    x8 = synth.uniform_ci8(300, 2, 50, seed=5, lo=-127, hi=127)
+    got, _ = run(torch, x8.astype(np.float32), "tensor", fmt="cf32")
+    assert np.array_equal(got.astype(np.float64), oracle.correlate(oracle.FMT_CI8, x8).astype(np.float64))
+
+
+def test_cf32_wide_fold_into_double(torch):
+    x = synth.gaussian_cf32(256, 2, 40, seed=8)
+    want = oracle.correlate(oracle.FMT_CF32, x)
+    xd = torch.from_numpy(x).cuda()
+    with xcorr.Plan(40, 2, 256, fmt="cf32") as plan:
+        wide = torch.zeros((2, plan.info["n_pairs"], 2), dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            plan.execute(xd)
+            plan.dump(out=wide, wide=True, reset=True)
+        plan.sync()
+    e, _ = normalised_error(wide.cpu().numpy() / 3.0, want, 80)
+    assert e.max() <= 1e-6
+
+
+# ------------------------------------------------------ tuning shapes ---
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("groups,x_streams", [(1, 1), (2, 1), (3, 2), (8, 2)])
+def test_every_launch_shape_is_exact(torch, variant, groups, x_streams):
+    x = synth.uniform_ci4(333, 9, 100, seed=variant * 10 + groups, lo=-8, hi=7)
+    got, _ = run(torch, x, "tensor", tuning=(variant, groups, x_streams))
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_every_launch_shape_ci8(torch, variant):
+    x = synth.uniform_ci8(500, 5, 70, seed=variant)
+    got, _ = run(torch, x, "tensor", fmt="ci8", tuning=(variant, 2, 2))
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI8, x))
+
+
+def test_autotune_keeps_results_exact(torch):
+    x = synth.uniform_ci4(256, 64, 128, seed=12, lo=-8, hi=7)
+    xd = torch.from_numpy(x).cuda()
+    with xcorr.Plan(128, 64, 256) as plan:
+        plan.execute(xd)  # an integration in progress is discarded by the autotuner
+        best, ms = plan.autotune(xd)
+        assert 0 <= best["stage_variant"] <= 2 and 1 <= best["groups"] <= 8 and ms > 0
+        assert plan.query()["samples_integrated"] == 0
+        assert plan.query()["tuning"]["stage_variant"] == best["stage_variant"]
+        plan.execute(xd)
+        got = plan.dump().cpu().numpy()
+        plan.sync()
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
 
 
 # ------------------------------------------------- full-size workloads ---
