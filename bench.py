@@ -50,6 +50,9 @@ WORKLOADS = {
     "cf32_512in": dict(name="512 inputs, 256 channels, K=4096, float32 complex (sigma 1)",
                        n_sta=256, n_chan=256, n_time=4096, seed=14018288 + 4, fmt="cf32",
                        gen="gauss32", dtype="bf16x3"),
+    # 24 independent subarrays of uneven size in one launch (see batch_arm)
+    "batch24": dict(name="24 subarrays, inputs 16..704, channels 64..1024, K 512..8192, 4+4-bit",
+                    seed=14018288 + 4, fmt="ci4", dtype="e4m3"),
 }
 WORKLOAD = WORKLOADS["ci4_512in"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "xcorr_tc_e4m3_512in_512ch_2048t.json")
@@ -70,6 +73,8 @@ def parse_args():
                     help="the default is the headline 512-input 4-bit workload")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shape")
+    ap.add_argument("--tuning", default="",
+                    help="fix the launch shape instead of autotuning: variant,groups,x_streams")
     return ap.parse_args()
 
 
@@ -230,6 +235,10 @@ def reference_arm(args) -> int:
     import oracle
     from paper_1401_8288_gb300 import costmodel
     oracle.build()
+    if args.workload == "batch24":
+        emit({"impl": "reference", "unavailable": "the oracle arm times single workloads; "
+              "run it per subarray size"})
+        return 0
     w = WORKLOADS[args.workload]
     x = make_input(w, w["seed"])
     ofmt = {"ci4": oracle.FMT_CI4, "ci8": oracle.FMT_CI8, "cf32": oracle.FMT_CF32}[w["fmt"]]
@@ -262,6 +271,83 @@ def reference_arm(args) -> int:
     return 0
 
 
+# ----------------------------------------------------------------- batch --
+def batch_arm(args) -> int:
+    """Many uneven subarrays: one persistent launch per step, replayed as a
+    CUDA graph, against the same subarrays run as separate plans."""
+    import torch
+
+    from paper_1401_8288_gb300 import dist
+    info = dist.init("nccl")
+    torch.cuda.set_device(info.local_rank)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1401_8288_gb300 import costmodel, synth, xcorr
+
+    w = WORKLOADS["batch24"]
+    subs = synth.subarray_batch(w["seed"])
+    sizes = [(s["n_sta"], s["n_chan"], s["n_time"]) for s in subs]
+    xs = [synth.uniform_ci4_torch(nt, nc, ns, seed=s["seed"] + info.rank) for (ns, nc, nt), s in zip(sizes, subs)]
+    cmacs = sum(costmodel.cmacs(nc, nt, 2 * ns) for ns, nc, nt in sizes)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, steps):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        dist.barrier()
+        ev0.record()
+        for _ in range(steps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return dist.max_over_ranks(ev0.elapsed_time(ev1), torch.device("cuda", info.local_rank)) / steps
+
+    batch = xcorr.Batch(sizes)
+    # autotuner: the stage ring of the batch launch, by replay time
+    best = None
+    for v in range(3):
+        batch.set_variant(v)
+        batch.capture(xs)
+        ms = timed(batch.replay, 3)
+        if best is None or ms < best[1]:
+            best = (v, ms)
+    batch.set_variant(best[0])
+    batch.capture(xs)
+    with ClockSampler(info.local_rank) as clocks:
+        ms_graph = timed(batch.replay, args.steps)
+    batch.sync()
+    outs = batch.outputs
+    # the same subarrays as separate plans, one after another
+    plans = [xcorr.Plan(ns, nc, nt) for ns, nc, nt in sizes]
+    per_out = [torch.empty_like(o) for o in outs]
+
+    def each():
+        for p, x, o in zip(plans, xs, per_out):
+            p.execute_dump(x, o)
+
+    ms_each = timed(each, max(2, args.steps // 4))
+    same = all(torch.equal(a, b) for a, b in zip(outs, per_out))
+    for p in plans:
+        p.close()
+    batch.close()
+    value = info.world * cmacs / (ms_graph * 1e-3) / 1e12
+    if info.rank == 0:
+        emit({"metric": METRIC, "value": value, "unit": "TCMAC/s", "n_gpus": info.world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3",
+              "data": "synthetic",
+              "config": {"workload": w["name"], "subarrays": sizes, "stage_variant": best[0],
+                         "graph": True, "cmacs_per_step_per_gpu": cmacs,
+                         "l2": "inputs larger than L2 (15.2 GB in, 7.5 GB out per step)"},
+              "per_instance": {"value": info.world * cmacs / (ms_each * 1e-3) / 1e12,
+                               "unit": "TCMAC/s", "ms_per_step": ms_each,
+                               "batch_speedup": ms_each / ms_graph, "outputs_identical": same},
+              "gpu_launches": (len(sizes) + 1) * args.steps, "clocks": clocks.summary()})
+    dist.barrier()
+    return 0
+
+
 # ------------------------------------------------------------------ ours --
 def our_arm(args) -> int:
     import torch
@@ -290,7 +376,11 @@ def our_arm(args) -> int:
     in_bytes, out_bytes = x.nbytes, n_chan * n_pairs * 8
 
     plan = xcorr.Plan(n_sta, n_chan, n_time, fmt=fmt, engine="tensor")
-    tuning, tune_ms = (plan.query()["tuning"], None) if args.no_autotune else plan.autotune(xd)
+    if args.tuning:
+        plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
+        tuning = plan.query()["tuning"]
+    else:
+        tuning, _ = (plan.query()["tuning"], None) if args.no_autotune else plan.autotune(xd)
     launches_per_step = plan.query()["kernels_per_execute"]  # unpack + X launches per channel group
     out_dtype = torch.float32 if fmt == "cf32" else torch.int32
     out = torch.empty((n_chan, n_pairs, 2), dtype=out_dtype, device=dev)
@@ -441,6 +531,8 @@ def main() -> int:
     args = parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batch24":
+        return batch_arm(args)
     return our_arm(args)
 
 

@@ -249,6 +249,46 @@ xcorr_status xcorr_correlate_ci4_noalloc(const void *d_in, int n_time, int n_cha
                                          int n_stations, void *d_out, int *d_status,
                                          void *stream);
 
+/*
+ * Batches: many independent 4-bit correlations of uneven size (each its own
+ * station count, channel count and integration length; Sec. 2.1: each
+ * sub-band is an independent X-stage) in one persistent tensor-core launch.
+ * Each execute unpacks every subarray, then runs one X launch over the union
+ * of their tile pairs, longest first, so small subarrays fill the tail of the
+ * large ones.  Subarray s correlates exactly cfgs[s].max_time_per_exec
+ * (<= 130,944) samples per execute from d_ins[s] ([t][c][s][2] CI4, device)
+ * into d_outs[s] (int32 [C][P][2], device, written, not added to).
+ * The batch owns each subarray's staging planes; the caller owns the buffers.
+ */
+typedef struct xcorr_batch_s *xcorr_batch;
+
+/* Errors: INVALID_ARG, UNSUPPORTED (a non-CI4 subarray, a device that is not
+ * sm_103a, more than 130,944 samples), BUDGET (sum of planes over the
+ * smallest nonzero hbm_budget_bytes), OOM, CUDA. */
+xcorr_status xcorr_batch_create(xcorr_batch *out, const xcorr_config *cfgs, int n);
+
+/* The stage ring of the batch launch (0, 1 or 2 as in xcorr_tuning). */
+xcorr_status xcorr_batch_set_variant(xcorr_batch batch, int stage_variant);
+
+/* One batch execute on the stream.  Errors: INVALID_ARG, CUDA. */
+xcorr_status xcorr_batch_execute(xcorr_batch batch, const void *const *d_ins, void *const *d_outs,
+                                 void *stream);
+
+/* Capture one batch execute with these buffers into a CUDA graph (the
+ * buffers must stay valid while the graph is replayed).  Errors: INVALID_ARG,
+ * CUDA. */
+xcorr_status xcorr_batch_capture(xcorr_batch batch, const void *const *d_ins, void *const *d_outs,
+                                 void *stream);
+
+/* Launch the captured graph on the stream.  Errors: INVALID_ARG, CUDA. */
+xcorr_status xcorr_batch_replay(xcorr_batch batch, void *stream);
+
+/* Wait for the stream and report kernel-side failures (DEVICE). */
+xcorr_status xcorr_batch_sync(xcorr_batch batch, void *stream);
+
+/* Synchronise the device and free the batch.  NULL is a no-op. */
+xcorr_status xcorr_batch_destroy(xcorr_batch batch);
+
 /* Synchronise the device, free the plan's memory and the plan.  NULL is a no-op. */
 xcorr_status xcorr_destroy(xcorr_plan plan);
 

@@ -324,6 +324,11 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
       return cuda_fail(e, "stream or event creation");
     }
   }
+  if (plan->exps && (e = cudaMemset(plan->exps, 0, exps_bytes)) != cudaSuccess) {
+    release(plan);
+    delete plan;
+    return cuda_fail(e, "exponent clear");
+  }
   if ((e = cudaMemset(plan->status, 0, 256)) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
     release(plan);
     delete plan;

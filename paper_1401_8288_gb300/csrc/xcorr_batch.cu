@@ -1,0 +1,278 @@
+// xcorr_batch.cu -- many independent correlations of uneven size in one
+// persistent tensor-core launch, optionally replayed as a CUDA graph.
+//
+// A batch holds n subarrays (each its own station count, channel count and
+// integration length, 4+4-bit input).  One execute unpacks every subarray
+// into its own E4M3 planes and then runs a single launch of the X kernel over
+// the union of their work items (subarray, channel, I, J), sorted longest
+// first and dealt round-robin to the persistent CTAs, so a large subarray's
+// tail is filled with the small ones' items instead of leaving SMs idle
+// between per-instance launches.  Sec. 2.1: each sub-band (here each
+// subarray) is an independent X-stage.
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "xcorr_internal.h"
+
+struct xcorr_batch_s {
+  int n = 0;
+  int device = 0, num_sms = 0;
+  int variant = 0;
+  std::vector<xcorr_config> cfg;
+  std::vector<int> n_inputs, ni_pad;
+  std::vector<int64_t> n_pairs;
+  std::vector<void*> planes;
+  xc::SubDescHost* descs_host = nullptr;  // n entries (pinned)
+  void* descs_dev = nullptr;
+  uint4* items_dev = nullptr;
+  int n_items = 0;
+  int* status = nullptr;
+  // graph replay
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+};
+
+namespace {
+
+xcorr_status bfail(xcorr_status st, const std::string& msg) { return xc::set_error(st, msg); }
+
+void batch_release(xcorr_batch b) {
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (void* p : b->planes)
+    if (p) cudaFree(p);
+  if (b->descs_dev) cudaFree(b->descs_dev);
+  if (b->items_dev) cudaFree(b->items_dev);
+  if (b->descs_host) cudaFreeHost(b->descs_host);
+  if (b->status) cudaFree(b->status);
+}
+
+// (Re)build the subarray descriptors and the item list for stage variant v
+// and the given output buffers.
+xcorr_status build_tables(xcorr_batch b, void* const* d_outs) {
+  const int kt = xc::tc_stage_samples(1, b->variant);
+  std::vector<uint4> items;
+  std::vector<int> cost;
+  for (int s = 0; s < b->n; ++s) {
+    const int n_time = b->cfg[s].max_time_per_exec;
+    std::string err;
+    if (!xc::encode_plane_tmap(&b->descs_host[s].tmap, b->planes[s], 1, b->n_inputs[s], b->ni_pad[s], n_time, n_time,
+                               2 * b->cfg[s].n_channels, kt, &err))
+      return bfail(XCORR_ERR_CUDA, err);
+    xc::SubDescHost& d = b->descs_host[s];
+    d.out = d_outs ? d_outs[s] : nullptr;
+    d.n_pairs = b->n_pairs[s];
+    d.n_inputs = b->n_inputs[s];
+    d.n_kt = (n_time + kt - 1) / kt;
+    d.n_tw = (d.n_kt + xc::kTcWindowCI4 / kt - 1) / (xc::kTcWindowCI4 / kt);
+    const int nb = (b->n_inputs[s] + 127) / 128;
+    for (int c = 0; c < b->cfg[s].n_channels; ++c)
+      for (int I = 0; I < nb; ++I)
+        for (int J = 0; J <= I; ++J) {
+          items.push_back(make_uint4((unsigned)s, (unsigned)c, (unsigned)I, (unsigned)J));
+          cost.push_back(d.n_kt);
+        }
+  }
+  // longest first: a stable sort keeps each subarray's items channel-major
+  std::vector<int> order(items.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  std::vector<uint4> sorted(items.size());
+  for (size_t k = 0; k < order.size(); ++k) sorted[k] = items[order[k]];
+  if (b->items_dev && (int)sorted.size() != b->n_items) {
+    cudaFree(b->items_dev);
+    b->items_dev = nullptr;
+  }
+  cudaError_t e;
+  if (!b->items_dev && (e = cudaMalloc(&b->items_dev, sorted.size() * sizeof(uint4))) != cudaSuccess)
+    return bfail(XCORR_ERR_OOM, std::string("item list: ") + cudaGetErrorString(e));
+  b->n_items = (int)sorted.size();
+  if ((e = cudaMemcpy(b->items_dev, sorted.data(), sorted.size() * sizeof(uint4), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(b->descs_dev, b->descs_host, sizeof(xc::SubDescHost) * b->n, cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+    return bfail(XCORR_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
+  return XCORR_OK;
+}
+
+// Enqueue one batch execute: every unpack, then one X launch.
+xcorr_status enqueue(xcorr_batch b, const void* const* d_ins, cudaStream_t s) {
+  cudaError_t e;
+  for (int k = 0; k < b->n; ++k) {
+    e = xc::launch_unpack_ci4_e4m3(static_cast<const uint8_t*>(d_ins[k]), static_cast<uint8_t*>(b->planes[k]),
+                                   b->cfg[k].max_time_per_exec, b->cfg[k].n_channels, b->n_inputs[k], b->ni_pad[k],
+                                   b->cfg[k].max_time_per_exec, b->num_sms, s);
+    if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("unpack launch: ") + cudaGetErrorString(e));
+  }
+  e = xc::launch_xcorr_tc_batch(b->descs_dev, b->items_dev, b->n_items, b->variant, b->status, b->num_sms, s);
+  if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("batch X launch: ") + cudaGetErrorString(e));
+  return XCORR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+xcorr_status xcorr_batch_create(xcorr_batch* out, const xcorr_config* cfgs, int n) {
+  if (!out || !cfgs || n < 1 || n > 4096) return bfail(XCORR_ERR_INVALID_ARG, "need out, cfgs and 1 <= n <= 4096");
+  *out = nullptr;
+  for (int s = 0; s < n; ++s) {
+    const xcorr_config& c = cfgs[s];
+    if (c.n_pols != 2 || c.n_stations < 1 || c.n_stations > (1 << 20) || c.n_channels < 1 ||
+        c.max_time_per_exec < 1)
+      return bfail(XCORR_ERR_INVALID_ARG, "subarray " + std::to_string(s) + ": invalid sizes");
+    if (c.fmt != XCORR_IN_CI4)
+      return bfail(XCORR_ERR_UNSUPPORTED, "batches take 4+4-bit subarrays (subarray " + std::to_string(s) + ")");
+    if (c.max_time_per_exec > xc::kTcWindowCI4)
+      return bfail(XCORR_ERR_UNSUPPORTED, "batch subarrays hold at most 130,944 samples per execute");
+  }
+  int dev = 0, major = 0, minor = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
+  if (major != 10 || minor != 3) return bfail(XCORR_ERR_UNSUPPORTED, "needs an sm_103a (GB300) device");
+
+  xcorr_batch b = new (std::nothrow) xcorr_batch_s();
+  if (!b) return bfail(XCORR_ERR_OOM, "host allocation failed");
+  b->n = n;
+  b->device = dev;
+  b->num_sms = sms;
+  b->cfg.assign(cfgs, cfgs + n);
+  size_t budget = 0, need = 0;
+  for (int s = 0; s < n; ++s) {
+    const int ni = 2 * cfgs[s].n_stations;
+    b->n_inputs.push_back(ni);
+    b->ni_pad.push_back((ni + 15) / 16 * 16);
+    b->n_pairs.push_back((int64_t)ni * (ni + 1) / 2);
+    need += (size_t)cfgs[s].n_channels * 2 * cfgs[s].max_time_per_exec * b->ni_pad.back();
+    if (cfgs[s].hbm_budget_bytes) budget = budget ? std::min(budget, cfgs[s].hbm_budget_bytes) : cfgs[s].hbm_budget_bytes;
+  }
+  if (budget && need > budget) {
+    delete b;
+    return bfail(XCORR_ERR_BUDGET, "the batch needs " + std::to_string(need) + " device bytes of planes, budget " +
+                                       std::to_string(budget));
+  }
+  b->planes.assign(n, nullptr);
+  for (int s = 0; s < n && e == cudaSuccess; ++s)
+    e = cudaMalloc(&b->planes[s], (size_t)cfgs[s].n_channels * 2 * cfgs[s].max_time_per_exec * b->ni_pad[s]);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b->descs_host), sizeof(xc::SubDescHost) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->descs_dev, sizeof(xc::SubDescHost) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->status, 256);
+  if (e == cudaSuccess) e = cudaMemset(b->status, 0, 256);
+  if (e != cudaSuccess) {
+    batch_release(b);
+    delete b;
+    cudaGetLastError();
+    return bfail(e == cudaErrorMemoryAllocation ? XCORR_ERR_OOM : XCORR_ERR_CUDA,
+                 std::string("batch allocation: ") + cudaGetErrorString(e));
+  }
+  xcorr_status st = build_tables(b, nullptr);
+  if (st != XCORR_OK) {
+    batch_release(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_batch_set_variant(xcorr_batch b, int stage_variant) {
+  if (!b || stage_variant < 0 || stage_variant >= xc::kTcVariants)
+    return bfail(XCORR_ERR_INVALID_ARG, "need a batch and stage_variant in [0, 2]");
+  b->variant = stage_variant;
+  if (b->graph_exec) {  // a captured graph holds the old shape
+    cudaGraphExecDestroy(b->graph_exec);
+    cudaGraphDestroy(b->graph);
+    b->graph_exec = nullptr;
+    b->graph = nullptr;
+  }
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_batch_execute(xcorr_batch b, const void* const* d_ins, void* const* d_outs, void* stream) {
+  if (!b || !d_ins || !d_outs) return bfail(XCORR_ERR_INVALID_ARG, "batch, d_ins and d_outs must not be NULL");
+  for (int s = 0; s < b->n; ++s)
+    if (!d_ins[s] || !d_outs[s]) return bfail(XCORR_ERR_INVALID_ARG, "a subarray buffer is NULL");
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  // the tables are rewritten only when the outputs or the variant changed
+  bool same = true;
+  for (int s = 0; s < b->n && same; ++s) same = (b->descs_host[s].out == d_outs[s]);
+  const int kt = xc::tc_stage_samples(1, b->variant);
+  same = same && b->descs_host[0].n_kt == (b->cfg[0].max_time_per_exec + kt - 1) / kt;
+  if (!same) {
+    cudaStreamSynchronize(static_cast<cudaStream_t>(stream));  // earlier launches read the tables
+    xcorr_status st = build_tables(b, d_outs);
+    if (st != XCORR_OK) return st;
+  }
+  return enqueue(b, d_ins, static_cast<cudaStream_t>(stream));
+}
+
+xcorr_status xcorr_batch_capture(xcorr_batch b, const void* const* d_ins, void* const* d_outs, void* stream) {
+  if (!b || !d_ins || !d_outs) return bfail(XCORR_ERR_INVALID_ARG, "batch, d_ins and d_outs must not be NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  xcorr_status st = build_tables(b, d_outs);
+  if (st != XCORR_OK) return st;
+  if (b->graph_exec) {
+    cudaGraphExecDestroy(b->graph_exec);
+    cudaGraphDestroy(b->graph);
+    b->graph_exec = nullptr;
+    b->graph = nullptr;
+  }
+  cudaStream_t cap = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess)
+    return bfail(XCORR_ERR_CUDA, std::string("capture stream: ") + cudaGetErrorString(e));
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    st = enqueue(b, d_ins, cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    if (st == XCORR_OK && e == cudaSuccess) {
+      e = cudaGraphInstantiate(&b->graph_exec, g, 0);
+      b->graph = g;
+    } else if (g) {
+      cudaGraphDestroy(g);
+    }
+  }
+  cudaStreamDestroy(cap);
+  if (st != XCORR_OK) return st;
+  if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  (void)s;
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_batch_replay(xcorr_batch b, void* stream) {
+  if (!b || !b->graph_exec) return bfail(XCORR_ERR_INVALID_ARG, "no captured graph: call xcorr_batch_capture first");
+  cudaError_t e = cudaGraphLaunch(b->graph_exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_batch_sync(xcorr_batch b, void* stream) {
+  if (!b) return bfail(XCORR_ERR_INVALID_ARG, "batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
+  int code = 0;
+  e = cudaMemcpy(&code, b->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+  if (code) return bfail(XCORR_ERR_DEVICE, "a batch kernel reported failure code " + std::to_string(code));
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_batch_destroy(xcorr_batch b) {
+  if (!b) return XCORR_OK;
+  cudaSetDevice(b->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  batch_release(b);
+  delete b;
+  if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("cudaDeviceSynchronize: ") + cudaGetErrorString(e));
+  return XCORR_OK;
+}
+
+}  // extern "C"

@@ -120,6 +120,18 @@ struct TcLaunch {
   int num_sms = 0;
 };
 int tc_stage_samples(int elem_bytes, int variant);
+
+// One subarray of a batch, as the batch X kernel reads it from device memory
+// (host and device share this layout; it inherits the tensor map's alignment).
+struct SubDescHost {
+  CUtensorMap tmap;  // its E4M3 planes
+  void* out;         // its int2 [C][P] visibilities
+  int64_t n_pairs;
+  int n_inputs, n_kt, n_tw, pad;
+};
+// One launch of the batch X kernel over items (subarray, channel, I, J).
+cudaError_t launch_xcorr_tc_batch(const void* subs, const uint4* items, int n_items, int variant, int* status,
+                                  int num_sms, cudaStream_t stream);
 cudaError_t launch_xcorr_tc(const CUtensorMap* tmap, const TcLaunch& launch, cudaStream_t stream);
 
 cudaError_t launch_xcorr_cuda_core(int fmt, const void* in, int n_time, int n_chan, int n_inputs,

@@ -38,10 +38,15 @@
 // Two accumulator buffers (512 columns) let the drain of one block overlap the
 // MMAs of the next.
 //
-// Warp roles (192 threads, one CTA per SM): warps 0-3 drain TMEM (thread =
-// accumulator row) through a shared-memory transpose that makes the global
-// stores row-contiguous; warp 4 is the TMA producer; warp 5 allocates TMEM and
-// issues the MMAs.  Every wait is bounded (see sm103_ptx.cuh).
+// Warp roles (320 threads, one CTA per SM): warps 0-7 drain TMEM -- thread =
+// accumulator row, warps w and w + 4 take the two 64-column halves of the same
+// 32 rows -- adding every block into running sums held in registers, and
+// write the finished tile once through a shared-memory transpose that makes
+// the global stores row-contiguous; warp 8 is the TMA producer; warp 9
+// allocates TMEM and issues the MMAs.  Every wait is bounded (sm103_ptx.cuh).
+#include <cstring>
+#include <type_traits>
+
 #include "sm103_ptx.cuh"
 #include "xcorr_internal.h"
 
@@ -49,11 +54,12 @@ namespace xc {
 namespace {
 
 constexpr int kBlk = 128;          // inputs per tile side
-constexpr int kEpiWarps = 4;
-constexpr int kThreads = 192;
-constexpr int kProducerWarp = 4;
-constexpr int kMmaWarp = 5;
-constexpr int kChunk = 16;         // accumulator columns per epilogue step
+constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, 64 columns each
+constexpr int kThreads = 320;
+constexpr int kProducerWarp = 8;
+constexpr int kMmaWarp = 9;
+constexpr int kCols = 64;          // tile columns held per epilogue thread (its row)
+constexpr int kChunk = 8;          // columns per shared-memory transpose step
 constexpr int kPitch = kChunk + 1; // 8-byte words per staged row
 constexpr int kAccCols = 256;      // [Re | -Im]
 constexpr uint32_t kTmemCols = 512;
@@ -92,6 +98,21 @@ struct TcParams {
   const int8_t* exps;    // float input: window exponents [C][exp_windows][ni_pad]
   int exp_windows, ni_pad;
   int8_t pair_p[8], pair_q[8];  // digit indices of each plane pair
+  // batch mode: items (subarray, channel, I, J), longest first
+  const SubDescHost* subs;
+  const uint4* items;
+  int n_batch_items;
+};
+
+// What one work item (a tile pair of one channel) needs.
+struct ItemView {
+  const CUtensorMap* tmap;
+  int zc;          // plane index of the item's channel, first plane
+  int chan;        // channel (single mode: within the plan)
+  int I, J;        // tile pair
+  int n_kt, n_tw;  // stages, windows
+  int n_inputs;
+  uint2* out_c;    // the channel's packed triangle
 };
 
 __device__ __forceinline__ void tile_pair(int p, int& I, int& J) {
@@ -102,6 +123,33 @@ __device__ __forceinline__ void tile_pair(int p, int& I, int& J) {
   J = p - i * (i + 1) / 2;
 }
 
+template <bool BATCH>
+__device__ __forceinline__ void view_item(const TcParams& p, const CUtensorMap* tmap0, int item, ItemView& v) {
+  if (BATCH) {
+    const uint4 it = p.items[item];
+    const SubDescHost& d = p.subs[it.x];
+    v.tmap = &d.tmap;
+    v.chan = static_cast<int>(it.y);
+    v.zc = 2 * v.chan;
+    v.I = static_cast<int>(it.z);
+    v.J = static_cast<int>(it.w);
+    v.n_kt = d.n_kt;
+    v.n_tw = d.n_tw;
+    v.n_inputs = d.n_inputs;
+    v.out_c = static_cast<uint2*>(d.out) + (int64_t)v.chan * d.n_pairs;
+  } else {
+    const int cl = item / p.n_tile_pairs;
+    tile_pair(item - cl * p.n_tile_pairs, v.I, v.J);
+    v.tmap = tmap0;
+    v.chan = p.chan0 + cl;
+    v.zc = v.chan * p.planes_per_chan;
+    v.n_kt = p.n_kt;
+    v.n_tw = p.n_tw;
+    v.n_inputs = p.n_inputs;
+    v.out_c = static_cast<uint2*>(p.out) + (int64_t)v.chan * p.n_pairs;
+  }
+}
+
 template <int ESIZE>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
   if (ESIZE == 1)
@@ -110,7 +158,7 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
     mma_f16(d, a, b, id, acc);
 }
 
-template <int ESIZE, int KT, int STAGES, bool FLOAT_OUT>
+template <int ESIZE, int KT, int STAGES, bool FLOAT_OUT, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
     xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TcParams p) {
   using G = Geometry<ESIZE, KT, STAGES>;
@@ -146,26 +194,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  const int n_items = p.n_chan * p.n_tile_pairs;
-  const int n_blocks = p.n_tw * p.n_pairs_k;  // drained blocks per item: (window, pair)
+  const int n_items = BATCH ? p.n_batch_items : p.n_chan * p.n_tile_pairs;
 
   if (warp == kProducerWarp) {
     if (lane == 0) {
-      prefetch_tmap(&tmap);
+      if (!BATCH) prefetch_tmap(&tmap);
       int s = 0;
       uint32_t ph = 0, filled = 0, fill_parity[STAGES] = {};
       bool ok = true;
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-        const int cl = item / p.n_tile_pairs;
-        const int zc = (p.chan0 + cl) * p.planes_per_chan;
+        ItemView v;
+        view_item<BATCH>(p, &tmap, item, v);
+        const int zc = v.zc, I = v.I, J = v.J;
         const int half = p.planes_per_chan / 2;  // re planes, then im planes
-        int I, J;
-        tile_pair(item - cl * p.n_tile_pairs, I, J);
+        const int n_blocks = v.n_tw * p.n_pairs_k;  // drained blocks: (window, pair)
         for (int blk = 0; ok && blk < n_blocks; ++blk) {
           const int w = blk / p.n_pairs_k, pk = blk - w * p.n_pairs_k;
           const int pp = p.pair_p[pk], pq = p.pair_q[pk];
           const bool shared = (I == J) && (pp == pq);
-          const int tb1 = min(p.n_kt, (w + 1) * p.spw);
+          const int tb1 = min(v.n_kt, (w + 1) * p.spw);
         for (int tb = w * p.spw; tb < tb1; ++tb) {
           const int t0 = tb * KT;
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
@@ -177,11 +224,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int ch = 0; ch < G::kChunksPerTile; ++ch) {
             const int xi = I * kBlk + ch * (128 / ESIZE), xj = J * kBlk + ch * (128 / ESIZE);
-            tma_load_3d(st + ch * G::kChunkBytes, &tmap, &full[s], xi, t0, zc + pp);
-            tma_load_3d(st + G::kTileBytes + ch * G::kChunkBytes, &tmap, &full[s], xi, t0, zc + half + pp);
+            tma_load_3d(st + ch * G::kChunkBytes, v.tmap, &full[s], xi, t0, zc + pp);
+            tma_load_3d(st + G::kTileBytes + ch * G::kChunkBytes, v.tmap, &full[s], xi, t0, zc + half + pp);
             if (!shared) {
-              tma_load_3d(st + 2 * G::kTileBytes + ch * G::kChunkBytes, &tmap, &full[s], xj, t0, zc + pq);
-              tma_load_3d(st + 3 * G::kTileBytes + ch * G::kChunkBytes, &tmap, &full[s], xj, t0, zc + half + pq);
+              tma_load_3d(st + 2 * G::kTileBytes + ch * G::kChunkBytes, v.tmap, &full[s], xj, t0, zc + pq);
+              tma_load_3d(st + 3 * G::kTileBytes + ch * G::kChunkBytes, v.tmap, &full[s], xj, t0, zc + half + pq);
             }
           }
           fill_parity[s] = ph;
@@ -210,9 +257,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       int g = 0;  // windows processed by this CTA
       bool ok = true;
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-        const int cl = item / p.n_tile_pairs;
-        int I, J;
-        tile_pair(item - cl * p.n_tile_pairs, I, J);
+        ItemView v;
+        view_item<BATCH>(p, &tmap, item, v);
+        const int I = v.I, J = v.J;
+        const int n_blocks = v.n_tw * p.n_pairs_k;
         for (int blk = 0; ok && blk < n_blocks; ++blk, ++g) {
           const int w = blk / p.n_pairs_k, pk = blk - w * p.n_pairs_k;
           const bool shared = (I == J) && (p.pair_p[pk] == p.pair_q[pk]);
@@ -225,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t d = tmem + static_cast<uint32_t>(buf * kAccCols);
           const int kb0 = w * p.spw;
-          const int kb1 = min(p.n_kt, kb0 + p.spw);
+          const int kb1 = min(v.n_kt, kb0 + p.spw);
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&full[s], ph, abort_flag, p.status, DEV_TIMEOUT_FULL)) {
               ok = false;
@@ -262,17 +310,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(mma_done, 0, &never, p.status, DEV_TIMEOUT_DRAIN);
     }
   } else {
-    // Epilogue: warp w drains TMEM lanes 32w .. 32w + 31 (tile rows).
+    // Epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 (tile rows),
+    // columns 64 (w / 4) .. + 63; each thread keeps its row's running sums.
+    using Acc = typename std::conditional<FLOAT_OUT, float, int>::type;
     uint2* stage_rows = staging + warp * 32 * kPitch;
-    const int half = lane >> 4, col = lane & 15;
+    const int quarter = warp & 3, colh = warp >> 2;
     int g = 0;
     bool ok = true;
     for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-      const int cl = item / p.n_tile_pairs;
-      int I, J;
-      tile_pair(item - cl * p.n_tile_pairs, I, J);
-      uint2* out_c = static_cast<uint2*>(p.out) + (int64_t)(p.chan0 + cl) * p.n_pairs;
-      const int row0 = I * kBlk + warp * 32;  // first global input row of this warp
+      ItemView v;
+      view_item<BATCH>(p, &tmap, item, v);
+      const int n_inputs = v.n_inputs;
+      const int n_blocks = v.n_tw * p.n_pairs_k;
+      uint2* out_c = v.out_c;
+      const int row0 = v.I * kBlk + quarter * 32;  // first global input row of this warp
+      const int col0 = v.J * kBlk + colh * kCols;  // first global input column of this warp
+      const bool live = (row0 < n_inputs) && (col0 <= row0 + 31) && (col0 < n_inputs);
+      Acc acc_re[kCols], acc_im[kCols];
+#pragma unroll
+      for (int q = 0; q < kCols; ++q) acc_re[q] = acc_im[q] = Acc(0);
       for (int blk = 0; blk < n_blocks; ++blk, ++g) {
         const int buf = g & 1;
         const uint32_t use = static_cast<uint32_t>(g >> 1);
@@ -281,69 +337,107 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const bool add = (blk > 0) || p.accumulate_first;
-        // float input: this block's scale 2^(E_i + E_j - 12 - 8(p + q)), split
-        // into the row factor (E_i) and the column factors (E_j, per chunk)
+        // float input: this block's scale 2^(E_i + E_j - 12 - 8(p + q))
         const int8_t* exps_w = nullptr;
         float row_scale = 1.f;
         if (FLOAT_OUT) {
           const int w = blk / p.n_pairs_k, pk = blk - w * p.n_pairs_k;
-          exps_w = p.exps + ((int64_t)(p.chan0 + cl) * p.exp_windows + w) * p.ni_pad;
-          const int i_row = min(row0 + lane, p.n_inputs - 1);
+          exps_w = p.exps + ((int64_t)v.chan * p.exp_windows + w) * p.ni_pad;
+          const int i_row = min(row0 + lane, n_inputs - 1);
           row_scale = ldexpf(1.f, static_cast<int>(exps_w[i_row]) - 12 - 8 * (p.pair_p[pk] + p.pair_q[pk]));
         }
-        const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + buf * kAccCols;
-        for (int j0 = 0; j0 < kBlk; j0 += kChunk) {
-          uint32_t re[16], nim[16];
-          tmem_ld16(taddr + j0, re);
-          tmem_ld16(taddr + 128 + j0, nim);
-          tmem_ld_wait();
-          // skip chunks that lie wholly above the diagonal or past the inputs
-          const int jfirst = J * kBlk + j0;
-          const bool any = (jfirst <= row0 + 31) && (row0 < p.n_inputs);
-          if (any) {
+        const uint32_t taddr =
+            tmem + (static_cast<uint32_t>(quarter * 32) << 16) + buf * kAccCols + colh * kCols;
+        if (FLOAT_OUT) {
+          // exact integer block sums times an exact power of two; the column
+          // exponents of 8 columns come in one 8-byte load (padding entries
+          // are zero)
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              if (FLOAT_OUT) {
-                // exact integer block sums times an exact power of two
-                const int jq = min(jfirst + q, p.n_inputs - 1);
-                const float sc = ldexpf(row_scale, static_cast<int>(exps_w[jq]));
-                stage_rows[lane * kPitch + q] = make_uint2(__float_as_uint(__uint_as_float(re[q]) * sc),
-                                                           __float_as_uint(-__uint_as_float(nim[q]) * sc));
-              } else {
-                stage_rows[lane * kPitch + q] =
-                    make_uint2(static_cast<uint32_t>(__float2int_rn(__uint_as_float(re[q]))),
-                               static_cast<uint32_t>(-__float2int_rn(__uint_as_float(nim[q]))));
+          for (int k = 0; k < kCols / 8; ++k) {
+            uint32_t re[8], nim[8];
+            tmem_ld8(taddr + 8 * k, re);
+            tmem_ld8(taddr + 128 + 8 * k, nim);
+            tmem_ld_wait();
+            if (live) {
+              const uint2 e8 = *reinterpret_cast<const uint2*>(exps_w + col0 + 8 * k);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int ej = static_cast<int8_t>(((q < 4 ? e8.x : e8.y) >> (8 * (q & 3))) & 0xFF);
+                const float sc = ldexpf(row_scale, ej);
+                acc_re[8 * k + q] += __uint_as_float(re[q]) * sc;
+                acc_im[8 * k + q] -= __uint_as_float(nim[q]) * sc;
               }
             }
-            __syncwarp();
-#pragma unroll 4
-            for (int r = 0; r < 32; r += 2) {
-              const int rr = r + half;
-              const int i = row0 + rr;
-              const int j = jfirst + col;
-              if (i < p.n_inputs && j <= i) {
-                uint2 v = stage_rows[rr * kPitch + col];
-                uint2* dst = out_c + (int64_t)i * (i + 1) / 2 + j;
-                if (add) {
-                  const uint2 o = *dst;
-                  if (FLOAT_OUT) {
-                    v.x = __float_as_uint(__uint_as_float(v.x) + __uint_as_float(o.x));
-                    v.y = __float_as_uint(__uint_as_float(v.y) + __uint_as_float(o.y));
-                  } else {
-                    v.x += o.x;
-                    v.y += o.y;
-                  }
-                }
-                *dst = v;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < kCols / 8; ++k) {
+            uint32_t re[8], nim[8];
+            tmem_ld8(taddr + 8 * k, re);
+            tmem_ld8(taddr + 128 + 8 * k, nim);
+            tmem_ld_wait();
+            if (live) {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                acc_re[8 * k + q] += __float2int_rn(__uint_as_float(re[q]));
+                acc_im[8 * k + q] -= __float2int_rn(__uint_as_float(nim[q]));
               }
             }
-            __syncwarp();
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
+      }
+      if (!ok || !live) continue;
+      // Write the finished tile rows.  Per 8-column step a quarter-warp writes
+      // 8 consecutive pairs of one row (64 bytes); when adding into earlier
+      // integrations all loads of the lane are issued before its stores.
+      const bool add = p.accumulate_first != 0;
+      const int sub = lane >> 3, col = lane & 7;
+#pragma unroll
+      for (int ch = 0; ch < kCols / kChunk; ++ch) {
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+          Acc vr = acc_re[ch * kChunk + q], vi = acc_im[ch * kChunk + q];
+          stage_rows[lane * kPitch + q] = FLOAT_OUT ? make_uint2(__float_as_uint(vr), __float_as_uint(vi))
+                                                    : make_uint2(static_cast<uint32_t>(vr), static_cast<uint32_t>(vi));
+        }
+        __syncwarp();
+        const int j = col0 + ch * kChunk + col;
+        uint32_t valid = 0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int i = row0 + 4 * r + sub;
+          if (i < n_inputs && j <= i) valid |= 1u << r;
+        }
+        uint2 old[8];
+        if (add) {  // (continuing an integration: rarer, kept out of the register budget)
+#pragma unroll 1
+          for (int r = 0; r < 8; ++r) {
+            const int i = row0 + 4 * r + sub;
+            old[r] = (valid >> r) & 1u ? out_c[(int64_t)i * (i + 1) / 2 + j] : make_uint2(0u, 0u);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if ((valid >> r) & 1u) {
+            const int rr = 4 * r + sub;
+            const int i = row0 + rr;
+            uint2 v = stage_rows[rr * kPitch + col];
+            if (add) {
+              if (FLOAT_OUT) {
+                v.x = __float_as_uint(__uint_as_float(v.x) + __uint_as_float(old[r].x));
+                v.y = __float_as_uint(__uint_as_float(v.y) + __uint_as_float(old[r].y));
+              } else {
+                v.x += old[r].x;
+                v.y += old[r].y;
+              }
+            }
+            out_c[(int64_t)i * (i + 1) / 2 + j] = v;
+          }
+        }
+        __syncwarp();
       }
     }
   }
@@ -357,11 +451,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // One instantiation per (operand type, stage variant, output type) in use.
-template <int ESIZE, int V, bool FLOAT_OUT>
+template <int ESIZE, int V, bool FLOAT_OUT, bool BATCH = false>
 cudaError_t launch_variant(const CUtensorMap* tmap, const TcParams& p, int grid, cudaStream_t stream) {
   constexpr int KT = stage_rows_of(V, ESIZE), S = stages_of(V);
   using G = Geometry<ESIZE, KT, S>;
-  auto kern = xcorr_tc_kernel<ESIZE, KT, S, FLOAT_OUT>;
+  auto kern = xcorr_tc_kernel<ESIZE, KT, S, FLOAT_OUT, BATCH>;
   static int attr_device = -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -378,6 +472,29 @@ cudaError_t launch_variant(const CUtensorMap* tmap, const TcParams& p, int grid,
 }  // namespace
 
 int tc_stage_samples(int elem_bytes, int variant) { return stage_rows_of(variant, elem_bytes); }
+
+cudaError_t launch_xcorr_tc_batch(const void* subs, const uint4* items, int n_items, int variant, int* status,
+                                  int num_sms, cudaStream_t stream) {
+  const int kt = stage_rows_of(variant, 1);
+  TcParams p{};
+  p.n_pairs_k = 1;
+  p.spw = kTcWindowCI4 / kt;
+  p.planes_per_chan = 2;
+  p.accumulate_first = 0;
+  p.status = status;
+  p.subs = static_cast<const SubDescHost*>(subs);
+  p.items = items;
+  p.n_batch_items = n_items;
+  const int grid = n_items < num_sms ? n_items : num_sms;
+  if (grid < 1) return cudaSuccess;
+  CUtensorMap unused;
+  std::memset(&unused, 0, sizeof(unused));
+  switch (variant) {
+    case 0: return launch_variant<1, 0, false, true>(&unused, p, grid, stream);
+    case 1: return launch_variant<1, 1, false, true>(&unused, p, grid, stream);
+    default: return launch_variant<1, 2, false, true>(&unused, p, grid, stream);
+  }
+}
 
 cudaError_t launch_xcorr_tc(const CUtensorMap* tmap, const TcLaunch& L, cudaStream_t stream) {
   const int nb = (L.n_inputs + kBlk - 1) / kBlk;

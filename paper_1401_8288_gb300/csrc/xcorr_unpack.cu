@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(256) unpack_cf32_digits_kernel(const float2* _
     const int c = c0 + static_cast<int>(rest / n_w);
     const int t0 = w * window, t1 = min(n_time, t0 + window);
     float mx = 0.f;
+#pragma unroll 8
     for (int t = t0; t < t1; ++t) {
       const float2 v = __ldg(in + ((int64_t)t * n_chan + c) * n_inputs + i);
       mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
@@ -256,6 +257,7 @@ __global__ void __launch_bounds__(256) unpack_cf32_digits_kernel(const float2* _
     exps[((int64_t)c * exp_windows + w) * ni_pad + i] = static_cast<int8_t>(e);
     const float scale = ldexpf(1.f, 22 - e);
     uint16_t* base = planes + (6 * (int64_t)c) * comp_stride + i;
+#pragma unroll 4
     for (int t = t0; t < t1; ++t) {
       const float2 v = __ldg(in + ((int64_t)t * n_chan + c) * n_inputs + i);
       uint16_t dr[3], dm[3];

@@ -183,3 +183,17 @@ def planewave_phases(n_chan: int, n_sta: int, seed: int) -> np.ndarray:
     """The per-station phases [chan][sta] that ``gaussian_planewave_ci4`` gives
     its common source for the same seed (they are its first draws)."""
     return _delay_phases(_rng(seed), n_chan, n_sta)
+
+
+def uniform_ci4_torch(n_time: int, n_chan: int, n_sta: int, seed: int, device: str = "cuda",
+                      lo: int = -7, hi: int = 7):
+    """Like ``uniform_ci4`` but drawn on the device with torch's Philox
+    generator (a different stream from the numpy one, same distribution):
+    for large timing inputs.  Returns a uint8 tensor [n_time][n_chan][n_sta][2]."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    shape = (n_time, n_chan, n_sta, 2)
+    re = torch.randint(lo, hi + 1, shape, generator=g, device=device, dtype=torch.int16)
+    im = torch.randint(lo, hi + 1, shape, generator=g, device=device, dtype=torch.int16)
+    return (((re & 0xF) << 4) | (im & 0xF)).to(torch.uint8)

@@ -30,7 +30,9 @@ ENGINES = {"auto": XCORR_ENGINE_AUTO, "tensor": XCORR_ENGINE_TENSOR,
 EXPORTS = ("xcorr_plan_create", "xcorr_execute", "xcorr_dump", "xcorr_sync", "xcorr_plan_query",
            "xcorr_destroy", "xcorr_last_error", "xcorr_baseline_index", "xcorr_profile_enable",
            "xcorr_profile_read", "xcorr_measure_peak", "xcorr_correlate_ci4_noalloc",
-           "xcorr_execute_dump", "xcorr_plan_set_tuning", "xcorr_autotune")
+           "xcorr_execute_dump", "xcorr_plan_set_tuning", "xcorr_autotune", "xcorr_batch_create",
+           "xcorr_batch_set_variant", "xcorr_batch_execute", "xcorr_batch_capture",
+           "xcorr_batch_replay", "xcorr_batch_sync", "xcorr_batch_destroy")
 PEAK_KINDS = {"tc_e4m3": 0, "tc_bf16": 1, "mma_sync_s8": 2, "dp4a": 3}
 
 
@@ -92,6 +94,13 @@ def load():
                 "xcorr_measure_peak": [i, ctypes.POINTER(ctypes.c_double)],
                 "xcorr_correlate_ci4_noalloc": [vp, i, i, i, vp, vp, vp],
                 "xcorr_plan_set_tuning": [vp, ctypes.POINTER(xcorr_tuning)],
+                "xcorr_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(xcorr_config), i],
+                "xcorr_batch_set_variant": [vp, i],
+                "xcorr_batch_execute": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp],
+                "xcorr_batch_capture": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp],
+                "xcorr_batch_replay": [vp, vp],
+                "xcorr_batch_sync": [vp, vp],
+                "xcorr_batch_destroy": [vp],
                 "xcorr_autotune": [vp, vp, i, vp, ctypes.POINTER(xcorr_tuning),
                                    ctypes.POINTER(ctypes.c_float)],
             }
@@ -210,6 +219,95 @@ def xcorr_correlate_ci4_noalloc(d_in: int, n_time: int, n_channels: int, n_stati
     share one fixed scratch array per GPU, so overlapping calls race."""
     _check(load().xcorr_correlate_ci4_noalloc(d_in, n_time, n_channels, n_stations, d_out,
                                               d_status or None, stream))
+
+
+def _ptrs(values) -> ctypes.Array:
+    return (ctypes.c_void_p * len(values))(*values)
+
+
+def xcorr_batch_create(subarrays: list[tuple[int, int, int]]) -> ctypes.c_void_p:
+    """subarrays: (n_stations, n_channels, n_time) of 4+4-bit correlations."""
+    cfgs = (xcorr_config * len(subarrays))(
+        *[xcorr_config(ns, 2, nc, nt, XCORR_IN_CI4, XCORR_ENGINE_TENSOR, 0) for ns, nc, nt in subarrays])
+    b = ctypes.c_void_p()
+    _check(load().xcorr_batch_create(ctypes.byref(b), cfgs, len(subarrays)))
+    return b
+
+
+def xcorr_batch_set_variant(batch, stage_variant: int) -> None:
+    _check(load().xcorr_batch_set_variant(batch, stage_variant))
+
+
+def xcorr_batch_execute(batch, d_ins: list[int], d_outs: list[int], stream: int = 0) -> None:
+    _check(load().xcorr_batch_execute(batch, _ptrs(d_ins), _ptrs(d_outs), stream))
+
+
+def xcorr_batch_capture(batch, d_ins: list[int], d_outs: list[int], stream: int = 0) -> None:
+    _check(load().xcorr_batch_capture(batch, _ptrs(d_ins), _ptrs(d_outs), stream))
+
+
+def xcorr_batch_replay(batch, stream: int = 0) -> None:
+    _check(load().xcorr_batch_replay(batch, stream))
+
+
+def xcorr_batch_sync(batch, stream: int = 0) -> None:
+    _check(load().xcorr_batch_sync(batch, stream))
+
+
+def xcorr_batch_destroy(batch) -> None:
+    _check(load().xcorr_batch_destroy(batch))
+
+
+class Batch:
+    """Several 4+4-bit correlations of uneven size in one tensor-core launch.
+
+    ``subarrays`` lists (n_stations, n_channels, n_time); ``execute(inputs)``
+    takes one CUDA tensor per subarray and returns the int32 [C][P][2] outputs.
+    """
+
+    def __init__(self, subarrays: list[tuple[int, int, int]]):
+        import torch
+        self._torch = torch
+        self.subarrays = list(subarrays)
+        self.handle = xcorr_batch_create(self.subarrays)
+        self.outputs = [torch.empty((nc, (2 * ns) * (2 * ns + 1) // 2, 2), dtype=torch.int32,
+                                    device="cuda") for ns, nc, _ in self.subarrays]
+
+    def _stream(self, stream) -> int:
+        if stream is None:
+            return self._torch.cuda.current_stream().cuda_stream
+        return getattr(stream, "cuda_stream", stream)
+
+    def set_variant(self, stage_variant: int) -> None:
+        xcorr_batch_set_variant(self.handle, stage_variant)
+
+    def execute(self, inputs, stream=None):
+        xcorr_batch_execute(self.handle, [x.data_ptr() for x in inputs],
+                            [o.data_ptr() for o in self.outputs], self._stream(stream))
+        return self.outputs
+
+    def capture(self, inputs, stream=None) -> None:
+        self._captured = list(inputs)  # the graph reads these buffers
+        xcorr_batch_capture(self.handle, [x.data_ptr() for x in inputs],
+                            [o.data_ptr() for o in self.outputs], self._stream(stream))
+
+    def replay(self, stream=None):
+        xcorr_batch_replay(self.handle, self._stream(stream))
+        return self.outputs
+
+    def sync(self, stream=None) -> None:
+        xcorr_batch_sync(self.handle, self._stream(stream))
+
+    def close(self) -> None:
+        if self.handle is not None:
+            xcorr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Plan:

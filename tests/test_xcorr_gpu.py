@@ -341,6 +341,51 @@ def test_autotune_keeps_results_exact(torch):
     assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
 
 
+# ------------------------------------------------------------- batches ---
+
+def batch_inputs(sizes, seed):
+    return [synth.uniform_ci4(nt, nc, ns, seed=seed + k, lo=-8, hi=7)
+            for k, (ns, nc, nt) in enumerate(sizes)]
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_batch_uneven_subarrays_bit_exact(torch, variant):
+    # uneven station, channel and sample counts, ragged tiles, one launch
+    sizes = [(8, 3, 512), (70, 2, 200), (200, 1, 385), (1, 4, 33), (140, 2, 1024)]
+    xs = batch_inputs(sizes, 100 * variant)
+    with xcorr.Batch(sizes) as batch:
+        batch.set_variant(variant)
+        outs = batch.execute([torch.from_numpy(x).cuda() for x in xs])
+        batch.sync()
+        for x, o in zip(xs, outs):
+            assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, x))
+
+
+def test_batch_graph_replay(torch):
+    sizes = [(16, 2, 256), (64, 3, 512), (100, 1, 128)]
+    xs = batch_inputs(sizes, 7)
+    ys = batch_inputs(sizes, 8)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    with xcorr.Batch(sizes) as batch:
+        batch.capture(xd)
+        for _ in range(3):
+            outs = batch.replay()
+        batch.sync()
+        for x, o in zip(xs, outs):
+            assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, x))
+        for dst, y in zip(xd, ys):  # the graph reads the same buffers: new data, new result
+            dst.copy_(torch.from_numpy(y).cuda())
+        outs = batch.replay()
+        batch.sync()
+        for y, o in zip(ys, outs):
+            assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, y))
+
+
+def test_batch_rejects_what_it_does_not_serve(torch):
+    with pytest.raises(xcorr.XcorrError):
+        xcorr.Batch([(8, 2, 200000)])  # more than one window per execute
+
+
 # ------------------------------------------------- full-size workloads ---
 
 def sample_check(got, x, fmt, channels, n_pairs_sample, seed):
