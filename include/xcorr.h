@@ -93,6 +93,10 @@ typedef struct {
     int stage_variant;  /* shared-memory ring: 0 = 3 x 64 KB, 1 = 4 x 48 KB, 2 = 6 x 32 KB stages */
     int groups;         /* channel groups whose unpack overlaps the X kernel; 0 = automatic (<= 8) */
     int x_streams;      /* 1 or 2 streams the groups' X launches alternate over                 */
+    int unfused;        /* 4-bit input: 0 = unpack on chip inside the X kernel where possible
+                           (N_i % 16 == 0, 16-byte aligned input, n_time <= 130,944;
+                           stage_variant then picks 128, 96 or 64-sample stages),
+                           1 = always through E4M3 planes in HBM                            */
 } xcorr_tuning;
 
 /* Opaque to the caller except through these fields (xcorr_plan_query). */

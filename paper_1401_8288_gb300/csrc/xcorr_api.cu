@@ -100,6 +100,13 @@ int tensor_groups(xcorr_plan plan) {
   return g < 1 ? 1 : static_cast<int>(g);
 }
 
+// The 4-bit tensor path can unpack on chip: inputs a multiple of 16 (TMA row
+// strides), a 16-byte aligned pointer and one exact block per tile pair.
+bool fused_applies(xcorr_plan plan, const void* d_in, int n_time) {
+  return plan->cfg.fmt == XCORR_IN_CI4 && !plan->tune_unfused && plan->n_inputs % 16 == 0 &&
+         reinterpret_cast<uintptr_t>(d_in) % 16 == 0 && n_time <= xc::kTcWindowCI4;
+}
+
 // Unpack channels [c0, c0 + nc) of the input into the plan's planes.
 cudaError_t unpack_group(xcorr_plan plan, const void* d_in, int n_time, int c0, int nc, cudaStream_t s) {
   const int C = plan->cfg.n_channels, N = plan->n_inputs, T = plan->cfg.max_time_per_exec;
@@ -129,7 +136,25 @@ xcorr_status run_execute(xcorr_plan plan, const void* d_in, int n_time, void* ta
     ev = plan->prof_events + xc::kProfileEvents * slot;
     if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return cuda_fail(e, "profile event");
   }
-  if (plan->engine == XCORR_ENGINE_TENSOR) {
+  if (plan->engine == XCORR_ENGINE_TENSOR && fused_applies(plan, d_in, n_time)) {
+    // 4-bit input with the unpack on chip: one launch on the caller's stream
+    const int variant = plan->tune_variant;
+    if (plan->raw_in != d_in || plan->raw_ntime != n_time || plan->raw_variant != variant) {
+      std::string err;
+      if (!xc::encode_raw_ci4_tmap(&plan->raw_tmap, d_in, N, C, n_time, xc::fused_stage_samples(variant), &err))
+        return fail(XCORR_ERR_CUDA, err);
+      plan->raw_in = d_in;
+      plan->raw_ntime = n_time;
+      plan->raw_variant = variant;
+    }
+    if (ev && ((e = cudaEventRecord(ev[1], s)) != cudaSuccess || (e = cudaEventRecord(ev[2], s)) != cudaSuccess))
+      return cuda_fail(e, "profile event");
+    e = xc::launch_xcorr_tc_fused_ci4(&plan->raw_tmap, variant, n_time, C, N, static_cast<int2*>(target),
+                                      !target_fresh, plan->status, plan->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused X kernel launch");
+    if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return cuda_fail(e, "profile event");
+    if (ev) plan->prof_ngroups[plan->prof_count % plan->prof_cap] = 1;
+  } else if (plan->engine == XCORR_ENGINE_TENSOR) {
     const int variant = plan->tune_variant;
     if (plan->tmap_ntime != n_time || plan->tmap_variant != variant) {
       std::string err;
@@ -435,10 +460,13 @@ xcorr_status xcorr_plan_query(xcorr_plan plan, xcorr_plan_info* info) {
   info->max_integration = plan->max_integration;
   info->device_bytes = plan->device_bytes;
   info->output_bytes = (size_t)plan->cfg.n_channels * plan->n_pairs * 8;
-  info->kernels_per_execute = plan->engine == XCORR_ENGINE_TENSOR ? 2 * tensor_groups(plan) : 1;
+  const bool fused = plan->engine == XCORR_ENGINE_TENSOR && plan->cfg.fmt == XCORR_IN_CI4 && !plan->tune_unfused &&
+                     plan->n_inputs % 16 == 0 && plan->cfg.max_time_per_exec <= xc::kTcWindowCI4;
+  info->kernels_per_execute = fused ? 1 : plan->engine == XCORR_ENGINE_TENSOR ? 2 * tensor_groups(plan) : 1;
   info->tuning.stage_variant = plan->tune_variant;
-  info->tuning.groups = tensor_groups(plan);
+  info->tuning.groups = fused ? 1 : tensor_groups(plan);
   info->tuning.x_streams = plan->tune_x_streams;
+  info->tuning.unfused = plan->tune_unfused;
   return XCORR_OK;
 }
 
@@ -450,9 +478,11 @@ xcorr_status xcorr_plan_set_tuning(xcorr_plan plan, const xcorr_tuning* t) {
     return fail(XCORR_ERR_INVALID_ARG, "stage_variant must be in [0, 2]");
   if (t->groups < 0 || t->groups > xc::kMaxGroups) return fail(XCORR_ERR_INVALID_ARG, "groups must be in [0, 8]");
   if (t->x_streams != 1 && t->x_streams != 2) return fail(XCORR_ERR_INVALID_ARG, "x_streams must be 1 or 2");
+  if (t->unfused != 0 && t->unfused != 1) return fail(XCORR_ERR_INVALID_ARG, "unfused must be 0 or 1");
   plan->tune_variant = t->stage_variant;
   plan->tune_groups = t->groups;
   plan->tune_x_streams = t->x_streams;
+  plan->tune_unfused = t->unfused;
   return XCORR_OK;
 }
 
@@ -463,7 +493,7 @@ xcorr_status xcorr_autotune(xcorr_plan plan, const void* d_in, int n_time, void*
   if (!d_in || n_time < 1 || n_time > plan->cfg.max_time_per_exec)
     return fail(XCORR_ERR_INVALID_ARG, "d_in must be set and n_time in [1, max_time_per_exec]");
   if (plan->engine != XCORR_ENGINE_TENSOR) {  // nothing to tune
-    if (best) *best = xcorr_tuning{plan->tune_variant, plan->tune_groups, plan->tune_x_streams};
+    if (best) *best = xcorr_tuning{plan->tune_variant, plan->tune_groups, plan->tune_x_streams, plan->tune_unfused};
     if (best_ms) *best_ms = 0.f;
     return XCORR_OK;
   }
@@ -478,15 +508,22 @@ xcorr_status xcorr_autotune(xcorr_plan plan, const void* d_in, int n_time, void*
   const int saved_cap = plan->prof_cap;
   plan->prof_cap = 0;  // candidates are not profiled
   const int group_choices[] = {1, 2, 4, 8};
-  xcorr_tuning winner{plan->tune_variant, plan->tune_groups, plan->tune_x_streams};
+  xcorr_tuning winner{plan->tune_variant, plan->tune_groups, plan->tune_x_streams, plan->tune_unfused};
   float winner_ms = 1e30f;
+  // candidates: the fused 4-bit kernel (3 stage shapes) where it applies, then
+  // every planes-based shape
+  plan->tune_unfused = 0;
+  const bool fused_ok = fused_applies(plan, d_in, n_time);
+  for (int uf = fused_ok ? 0 : 1; uf <= 1 && st == XCORR_OK; ++uf)
   for (int v = 0; v < xc::kTcVariants && st == XCORR_OK; ++v) {
     for (int gi = 0; gi < 4 && st == XCORR_OK; ++gi) {
       for (int xs = 1; xs <= 2 && st == XCORR_OK; ++xs) {
         if (group_choices[gi] == 1 && xs == 2) continue;  // one group has one X launch
+        if (uf == 0 && (gi > 0 || xs > 1)) continue;      // the fused kernel is one launch
         plan->tune_variant = v;
         plan->tune_groups = group_choices[gi];
         plan->tune_x_streams = xs;
+        plan->tune_unfused = uf;
         float best_rep = 1e30f;
         for (int rep = 0; rep < 3 && st == XCORR_OK; ++rep) {  // the first run warms up
           cudaEventRecord(e0, s);
@@ -503,7 +540,7 @@ xcorr_status xcorr_autotune(xcorr_plan plan, const void* d_in, int n_time, void*
         }
         if (st == XCORR_OK && best_rep < winner_ms) {
           winner_ms = best_rep;
-          winner = xcorr_tuning{v, group_choices[gi], xs};
+          winner = xcorr_tuning{v, group_choices[gi], xs, uf};
         }
       }
     }
@@ -517,6 +554,7 @@ xcorr_status xcorr_autotune(xcorr_plan plan, const void* d_in, int n_time, void*
   plan->tune_variant = winner.stage_variant;
   plan->tune_groups = winner.groups;
   plan->tune_x_streams = winner.x_streams;
+  plan->tune_unfused = winner.unfused;
   if (st != XCORR_OK) return st;
   if (best) *best = winner;
   if (best_ms) *best_ms = winner_ms;

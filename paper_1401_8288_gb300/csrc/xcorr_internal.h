@@ -69,6 +69,11 @@ struct xcorr_plan_s {
   int tune_variant = 0;        // stage shape, 0 .. kTcVariants - 1
   int tune_groups = 0;         // channel groups, 0 = heuristic
   int tune_x_streams = 2;      // X launches alternate over 1 or 2 streams
+  int tune_unfused = 0;        // 4-bit input: 1 = always through planes, 0 = fuse the unpack when possible
+
+  CUtensorMap raw_tmap{};      // fused 4-bit path: the caller's input, for raw_* below
+  const void* raw_in = nullptr;
+  int raw_ntime = -1, raw_variant = -1;
 
   CUtensorMap tmap{};          // planes, for tmap_ntime / tmap_variant
   int tmap_ntime = -1;
@@ -150,6 +155,15 @@ cudaError_t launch_fold_wide_i64(const int2* acc, int64_t* out, int64_t n_pairs_
 // input, time, channel * planes_per_chan + plane), box 128 bytes x box_t rows.
 bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inputs, int ni_pad,
                        int n_time, int max_time, int n_planes_total, int box_t, std::string* err);
+
+// Tensor map over the caller's CI4 input [t][c][i] (needs n_inputs % 16 == 0 and
+// a 16-byte aligned pointer): boxes of 128 inputs x 1 channel x box_t samples.
+bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int n_time, int box_t,
+                         std::string* err);
+// The fused 4-bit X kernel (unpack on chip); n_time <= kTcWindowCI4.
+int fused_stage_samples(int variant);
+cudaError_t launch_xcorr_tc_fused_ci4(const CUtensorMap* raw_map, int variant, int n_time, int n_chan, int n_inputs,
+                                      int2* out, bool accumulate, int* status, int num_sms, cudaStream_t stream);
 
 // int8 (re, im) samples -> two BF16 planes [c][2][t][ni_pad] (exact).
 cudaError_t launch_unpack_ci8_bf16(const int8_t* in, uint16_t* planes, int n_time, int n_chan, int c0,

@@ -14,32 +14,11 @@
 
 #include <cstring>
 
+#include "ci4_decode.cuh"
 #include "xcorr_internal.h"
 
 namespace xc {
 namespace {
-
-// E4M3 codes of 0..7 and of -8..-1, four per word, lowest byte first.
-constexpr uint32_t kPos0 = 0x44403800u;  // 0, 1, 2, 3
-constexpr uint32_t kPos1 = 0x4E4C4A48u;  // 4, 5, 6, 7
-constexpr uint32_t kNeg0 = 0xCACCCED0u;  // -8, -7, -6, -5
-constexpr uint32_t kNeg1 = 0xB8C0C4C8u;  // -4, -3, -2, -1
-
-// Byte-wise table lookup: `lo3` holds a 3-bit index in the low bits of each
-// byte, `neg` is 0xFF in the bytes whose 4-bit code is negative.
-__device__ __forceinline__ uint32_t e4m3_of_nibbles(uint32_t lo3, uint32_t neg) {
-  uint32_t sel = lo3 | (lo3 >> 4);                  // pack the four indices into 16 bits
-  sel = (sel & 0xFFu) | ((sel >> 8) & 0xFF00u);
-  const uint32_t pos = __byte_perm(kPos0, kPos1, sel);
-  const uint32_t ngt = __byte_perm(kNeg0, kNeg1, sel);
-  return (ngt & neg) | (pos & ~neg);
-}
-
-// Four CI4 samples (one per byte) -> four E4M3 real parts and four imaginary parts.
-__device__ __forceinline__ void ci4_to_e4m3(uint32_t v, uint32_t& re, uint32_t& im) {
-  re = e4m3_of_nibbles((v >> 4) & 0x07070707u, ((v >> 7) & 0x01010101u) * 0xFFu);
-  im = e4m3_of_nibbles(v & 0x07070707u, ((v >> 3) & 0x01010101u) * 0xFFu);
-}
 
 // Channels [c0, c0 + nc) of every time row, 16 inputs per thread (N_i a
 // multiple of 16 and a 16-byte aligned input); grid-stride over the rows.
@@ -151,6 +130,27 @@ bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inp
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     if (err) *err = "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r);
+    return false;
+  }
+  return true;
+}
+
+bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int n_time, int box_t,
+                         std::string* err) {
+  auto fn = encode_tiled_fn(err);
+  if (!fn) return false;
+  std::memset(map, 0, sizeof(*map));
+  // the caller's [t][c][i] bytes: dim0 input, dim1 channel, dim2 time; a box is
+  // 128 inputs x 1 channel x box_t samples = box_t rows of 128 bytes
+  cuuint64_t dims[3] = {(cuuint64_t)n_inputs, (cuuint64_t)n_chan, (cuuint64_t)n_time};
+  cuuint64_t strides[2] = {(cuuint64_t)n_inputs, (cuuint64_t)n_inputs * (cuuint64_t)n_chan};
+  cuuint32_t box[3] = {128, 1, (cuuint32_t)box_t};
+  cuuint32_t elem_strides[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(in), dims, strides, box, elem_strides,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (err) *err = "cuTensorMapEncodeTiled (raw input) failed with CUresult " + std::to_string((int)r);
     return false;
   }
   return true;

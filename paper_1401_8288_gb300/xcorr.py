@@ -51,7 +51,7 @@ class xcorr_config(ctypes.Structure):
 
 class xcorr_tuning(ctypes.Structure):
     _fields_ = [("stage_variant", ctypes.c_int), ("groups", ctypes.c_int),
-                ("x_streams", ctypes.c_int)]
+                ("x_streams", ctypes.c_int), ("unfused", ctypes.c_int)]
 
 
 class xcorr_plan_info(ctypes.Structure):
@@ -167,8 +167,9 @@ def xcorr_plan_query(plan) -> dict:
     return out
 
 
-def xcorr_plan_set_tuning(plan, stage_variant: int = 0, groups: int = 0, x_streams: int = 2) -> None:
-    t = xcorr_tuning(stage_variant, groups, x_streams)
+def xcorr_plan_set_tuning(plan, stage_variant: int = 0, groups: int = 0, x_streams: int = 2,
+                          unfused: int = 0) -> None:
+    t = xcorr_tuning(stage_variant, groups, x_streams, unfused)
     _check(load().xcorr_plan_set_tuning(plan, ctypes.byref(t)))
 
 
@@ -337,8 +338,9 @@ class Plan:
             return torch.float64 if wide else torch.float32
         return torch.int64 if wide else torch.int32
 
-    def set_tuning(self, stage_variant: int = 0, groups: int = 0, x_streams: int = 2) -> None:
-        xcorr_plan_set_tuning(self.handle, stage_variant, groups, x_streams)
+    def set_tuning(self, stage_variant: int = 0, groups: int = 0, x_streams: int = 2,
+                   unfused: int = 0) -> None:
+        xcorr_plan_set_tuning(self.handle, stage_variant, groups, x_streams, unfused)
 
     def autotune(self, x, stream=None) -> tuple[dict, float]:
         return xcorr_autotune(self.handle, x.data_ptr(), x.shape[0], self._stream(stream))

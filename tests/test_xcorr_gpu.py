@@ -314,8 +314,42 @@ def test_cf32_wide_fold_into_double(torch):
 @pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("groups,x_streams", [(1, 1), (2, 1), (3, 2), (8, 2)])
 def test_every_launch_shape_is_exact(torch, variant, groups, x_streams):
-    x = synth.uniform_ci4(333, 9, 100, seed=variant * 10 + groups, lo=-8, hi=7)
-    got, _ = run(torch, x, "tensor", tuning=(variant, groups, x_streams))
+    # 96 stations: N_i = 192 is a multiple of 16, so the planes path is forced
+    x = synth.uniform_ci4(333, 9, 96, seed=variant * 10 + groups, lo=-8, hi=7)
+    got, _ = run(torch, x, "tensor", tuning=(variant, groups, x_streams, 1))
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("n_sta,n_chan,n_time", [(8, 1, 1), (8, 2, 65), (64, 3, 300), (72, 2, 257),
+                                                 (200, 2, 385), (256, 3, 1000)])
+def test_fused_4bit_kernel_bit_exact(torch, variant, n_sta, n_chan, n_time):
+    # N_i a multiple of 16: the unpack runs inside the X kernel (raw TMA tiles
+    # decoded on chip); ragged input blocks and time tails
+    x = synth.uniform_ci4(n_time, n_chan, n_sta, seed=variant * 1000 + n_sta + n_time, lo=-8, hi=7)
+    got, _ = run(torch, x, "tensor", tuning=(variant, 0, 2, 0))
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+@pytest.mark.parametrize("unfused", [0, 1])
+def test_fused_and_planes_paths_agree_over_several_executes(torch, unfused):
+    chunks = [128, 77, 300, 5]
+    x = synth.uniform_ci4(sum(chunks), 4, 96, seed=31, lo=-8, hi=7)
+    got, n = run(torch, x, "tensor", chunks=chunks, tuning=(1, 0, 2, unfused))
+    assert n == sum(chunks)
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+def test_fused_falls_back_for_unaligned_input(torch):
+    # a pointer that is not 16-byte aligned takes the planes path, same result
+    x = synth.uniform_ci4(100, 2, 64, seed=3, lo=-8, hi=7)
+    raw = x.reshape(-1)
+    buf = torch.zeros(raw.size + 32, dtype=torch.uint8, device="cuda")
+    buf[3:3 + raw.size] = torch.from_numpy(raw).cuda()
+    with xcorr.Plan(64, 2, 100) as plan:
+        xcorr.xcorr_execute(plan.handle, buf.data_ptr() + 3, 100, 0)
+        got = plan.dump(stream=0).cpu().numpy().astype(np.int64)
+        plan.sync(0)
     assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
 
 
