@@ -53,9 +53,23 @@ WORKLOADS = {
     # 24 independent subarrays of uneven size in one launch (see batch_arm)
     "batch24": dict(name="24 subarrays, inputs 16..704, channels 64..1024, K 512..8192, 4+4-bit",
                     seed=14018288 + 4, fmt="ci4", dtype="e4m3"),
+    # the streaming server: F-engine packets -> device ring -> X-stage -> dumps (see stream_arm)
+    "stream1024": dict(name="1024 inputs (512 stations x 2 pols), 1024 channels, K=8192 per dump, "
+                            "4+4-bit Gaussian in 8 KB packets (4 samples x 128 channels x 16 "
+                            "inputs) + 16 B header, ring of 4 blocks of 2048 samples",
+                       n_sta=512, n_chan=1024, block=2048, blocks_per_dump=4, nt=4, nch=128, na=16,
+                       seed=14018288 + 5, fmt="ci4", dtype="e4m3"),
 }
 WORKLOAD = WORKLOADS["ci4_512in"]
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "xcorr_tc_e4m3_512in_512ch_2048t.json")
+# ncu DRAM traffic of the headline kernel per launch, stored beside the source hash it was taken on
+KERNEL_SOURCES = {
+    "xcorr_tc_fused_kernel": ("xcorr_tc_fused.cu", "sm103_ptx.cuh", "xcorr_internal.h"),
+    "xcorr_tc_kernel": ("xcorr_tc.cu", "sm103_ptx.cuh", "xcorr_internal.h"),
+}
+
+
+def profile_summary_path(kernel: str) -> str:
+    return os.path.join(ROOT, "profiles", f"{kernel}_512in_512ch_2048t.json")
 
 
 def parse_args():
@@ -162,22 +176,23 @@ def measured_peaks() -> dict:
     return {}
 
 
-def kernel_source_hash() -> str:
-    """Hash of the tensor X kernel's sources: a stored ncu traffic figure is
-    only reported while the kernel it was taken on is unchanged."""
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of a kernel's sources: a stored ncu traffic figure is only
+    reported while the kernel it was taken on is unchanged."""
     h = hashlib.sha256()
-    for name in ("xcorr_tc.cu", "sm103_ptx.cuh", "xcorr_internal.h"):
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1401_8288_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def stored_traffic() -> float | None:
-    if not os.path.exists(PROFILE_SUMMARY):
+def stored_traffic(kernel: str) -> float | None:
+    path = profile_summary_path(kernel)
+    if not os.path.exists(path):
         return None
-    with open(PROFILE_SUMMARY) as f:
+    with open(path) as f:
         s = json.load(f)
-    if s.get("source_hash") != kernel_source_hash():
+    if s.get("source_hash") != kernel_source_hash(kernel):
         return None
     return s.get("dram_bytes_per_launch")
 
@@ -381,7 +396,10 @@ def our_arm(args) -> int:
         tuning = plan.query()["tuning"]
     else:
         tuning, _ = (plan.query()["tuning"], None) if args.no_autotune else plan.autotune(xd)
-    launches_per_step = plan.query()["kernels_per_execute"]  # unpack + X launches per channel group
+    launches_per_step = plan.query()["kernels_per_execute"]  # all launches of one execute
+    fused = fmt == "ci4" and tuning["unfused"] == 0
+    x_kernel = "xcorr_tc_fused_kernel" if fused else "xcorr_tc_kernel"
+    x_launches = launches_per_step if fused else launches_per_step // 2  # else unpack + X per channel group
     out_dtype = torch.float32 if fmt == "cf32" else torch.int32
     out = torch.empty((n_chan, n_pairs, 2), dtype=out_dtype, device=dev)
 
@@ -485,8 +503,11 @@ def our_arm(args) -> int:
                              "uniform": "4+4-bit complex, uniform integers in [-7, 7]",
                              "gauss8": "int8 complex, Gaussian sigma 20 clipped to +-127",
                              "gauss32": "float32 complex, Gaussian sigma 1"}[w["gen"]],
-                   "engine": {"ci4": "tcgen05 kind::f8f6f4 (E4M3 codes of 4-bit integers, exact "
-                                     "FP32 TMEM sums drained to int32)",
+                   "engine": {"ci4": ("tcgen05 kind::f8f6f4, unpack fused on chip (offset-binary "
+                                      "E4M3 codes u = t + 8, exact FP32 TMEM sums, per-input sum "
+                                      "correction, int32 out)") if fused else
+                                     ("tcgen05 kind::f8f6f4 (E4M3 codes of 4-bit integers, exact "
+                                      "FP32 TMEM sums drained to int32)"),
                               "ci8": "tcgen05 kind::f16 (BF16 copies of int8 values, exact FP32 "
                                      "sums drained to int32 every 384 samples)",
                               "cf32": "tcgen05 kind::f16 (three BF16 pieces per value, six piece "
@@ -498,9 +519,9 @@ def our_arm(args) -> int:
                    "cmacs_per_step_per_gpu": cmacs_per_step},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": stored_traffic() if args.workload == "ci4_512in" else None,
-                     "kernel": "xcorr_tc_kernel", "ops_per_step": ops_per_step,
-                     "launches_per_step": launches_per_step // 2, "kernel_ms_per_step": x_ms,
+                     "traffic": stored_traffic(x_kernel) if args.workload == "ci4_512in" else None,
+                     "kernel": x_kernel, "ops_per_step": ops_per_step,
+                     "launches_per_step": x_launches, "kernel_ms_per_step": x_ms,
                      "peak_source": peak_note,
                      "frac_of_probe_peak": achieved / (peak_e4m3 if fmt == "ci4" else peak_e4m3 / 2)},
         "e2e": {"value": e2e_value, "unit": "TCMAC/s", "h2d_bytes_per_step": in_bytes,
@@ -515,9 +536,11 @@ def our_arm(args) -> int:
                       "speedup_tensor_vs_cuda_core": (value / info.world / cc_value)
                       if cc_value else None},
         "kernels_ms": {"unpack_span": unpack_ms, "x_tensor_sum": x_ms,
-                       "note": "per step: start to end of the last unpack, and the summed "
-                               "durations of the X launches (channel groups overlap the "
-                               "unpack of the next group with the X kernel of this one)"},
+                       "note": ("per step: the fused kernel has no separate unpack (span ~0); "
+                                "x_tensor_sum is its duration") if fused else
+                               ("per step: start to end of the last unpack, and the summed "
+                                "durations of the X launches (channel groups overlap the "
+                                "unpack of the next group with the X kernel of this one)")},
     }
     if info.rank == 0 and info.world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = oracle_sample(x, fmt, budget_s=12.0, n_pairs=n_pairs)
@@ -527,12 +550,117 @@ def our_arm(args) -> int:
     return 0
 
 
+def stream_arm(args) -> int:
+    """The streaming server of the paper's Fig. 4 on one GPU: an F-engine
+    emulator fills the stream's pinned landing chunks with packets, the stream
+    places them on the device, correlates each 2048-sample block and copies
+    every 8192-sample dump to host memory.  The emulator writes each chunk's
+    payloads once (one block of Gaussian samples) and then only advances the
+    headers' sequence numbers, the way a NIC would deliver packets by DMA
+    without the CPU touching the payload; so every block carries the same
+    samples and a dump must equal 4 x the block's correlation."""
+    import numpy as np
+    import torch
+
+    from paper_1401_8288_gb300 import dist
+    info = dist.init("nccl")
+    torch.cuda.set_device(info.local_rank)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1401_8288_gb300 import costmodel, synth, xcorr
+
+    w = WORKLOADS["stream1024"]
+    n_sta, n_chan, block, bpd = w["n_sta"], w["n_chan"], w["block"], w["blocks_per_dump"]
+    n_in = 2 * n_sta
+    n_groups, n_feng = n_chan // w["nch"], n_in // w["na"]
+    per_block = (block // w["nt"]) * n_groups * n_feng
+    chunks_per_block = 8
+    cfg = xcorr.stream_config(w["nt"], w["nch"], w["na"], block, n_blocks=4, blocks_per_dump=bpd,
+                              stack_threshold=per_block // 4, chunk_packets=per_block // chunks_per_block,
+                              n_chunks=chunks_per_block, n_host_dumps=2)
+    xd = synth.gaussian_ci4_torch(block, n_chan, n_sta, seed=w["seed"] + info.rank)
+    x = xd.cpu().numpy().reshape(block, n_chan, n_in)
+    plan = xcorr.Plan(n_sta, n_chan, block)
+    tuning = plan.query()["tuning"] if args.no_autotune else plan.autotune(xd)[0]
+    del xd
+    packets = xcorr.xcorr_packetize(x, cfg)
+    pb = xcorr.packet_bytes(cfg)
+    seq_per_block = (block // w["nt"]) * n_groups
+
+    stream = xcorr.Stream(plan, cfg)
+    views = {}
+
+    def push_block(b):
+        for k in range(chunks_per_block):
+            ptr, cap = stream.acquire()
+            if ptr not in views:  # first use of this chunk: write whole packets
+                views[ptr] = np.ctypeslib.as_array((ctypes.c_uint8 * (cap * pb)).from_address(ptr)).reshape(cap, pb)
+                views[ptr][:] = packets[k * cap:(k + 1) * cap]
+            hdr = views[ptr][:, :8].view(np.uint64)
+            hdr[:, 0] = packets[k * cap:(k + 1) * cap, :8].view(np.uint64)[:, 0] + np.uint64(b * seq_per_block)
+            stream.commit(cap)
+
+    warm_dumps = max(1, args.warmup // 4)
+    n_dumps = max(2, args.steps)
+    for b in range(warm_dumps * bpd):
+        push_block(b)
+    stream.wait_dump(warm_dumps - 1, timeout_ms=120000, copy=False)
+    torch.cuda.synchronize()
+    with ClockSampler(info.local_rank) as clocks:
+        t0 = time.perf_counter()
+        for b in range(warm_dumps * bpd, (warm_dumps + n_dumps) * bpd):
+            push_block(b)
+        recs = [stream.wait_dump(k, timeout_ms=120000, copy=False) for k in range(warm_dumps, warm_dumps + n_dumps)]
+        wall = time.perf_counter() - t0
+    last = stream.wait_dump(warm_dumps + n_dumps - 1, copy=True)
+    counters, _ = stream.counters()
+    stream.close()
+    plan.close()
+    # a sampled channel of the last dump against the oracle: 4 identical blocks
+    import oracle
+    c = 5
+    want = 4 * oracle.correlate(oracle.FMT_CI4, x[:, c:c + 1].reshape(block, 1, n_sta, 2))
+    exact = bool(np.array_equal(last["data"][c:c + 1].astype(np.int64), want))
+    payload_bytes = n_dumps * bpd * per_block * (pb - xcorr.XCORR_PACKET_HEADER_BYTES)
+    cmacs = n_dumps * bpd * costmodel.cmacs(n_chan, block, n_in)
+    lat = sorted(r["latency_ms"] for r in recs)
+    result = {
+        "metric": "streaming X-stage sustained input rate and dump latency",
+        "value": payload_bytes * 8 / wall / 1e9,
+        "unit": "Gbit/s",
+        "n_gpus": info.world,
+        "steps": n_dumps,
+        "warmup": warm_dumps,
+        "ms_per_step": 1e3 * wall / n_dumps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "e4m3",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "tuning": tuning, "step": "one dump (4 blocks)",
+                   "stack_threshold": cfg.stack_threshold, "chunk_packets": cfg.chunk_packets,
+                   "n_chunks": cfg.n_chunks},
+        "tcmacs": cmacs / wall / 1e12,
+        "dump_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                            "max": lat[-1]},
+        "packets": counters,
+        "sampled_channel_exact": exact,
+        "clocks": clocks.summary(),
+    }
+    if info.rank == 0:
+        emit(result)
+    dist.barrier()
+    return 0 if exact else 1
+
+
 def main() -> int:
     args = parse_args()
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "batch24":
         return batch_arm(args)
+    if args.workload == "stream1024":
+        return stream_arm(args)
     return our_arm(args)
 
 

@@ -293,6 +293,156 @@ xcorr_status xcorr_batch_sync(xcorr_batch batch, void *stream);
 /* Synchronise the device and free the batch.  NULL is a no-op. */
 xcorr_status xcorr_batch_destroy(xcorr_batch batch);
 
+/*
+ * Streaming: the receive side of the paper's X-stage server (Sec. 2.3,
+ * Sec. 2.4, Fig. 3, Fig. 4) on one GPU.  F-engine packets land in pinned host
+ * chunks, go to the device, and a scatter kernel places each payload by its
+ * (sequence number, F-engine id) into a device ring of n_blocks blocks of
+ * block_samples samples ([t][c][i] CI4, the layout xcorr_execute reads); that
+ * placement is the corner turn the paper's capture and unpack threads do.
+ * Packets may arrive in any order.  While the oldest block is incomplete,
+ * packets of later blocks are held in their own ring blocks (the paper's
+ * "stack"); when their number reaches stack_threshold, or a packet arrives for
+ * a block past the ring, the oldest block is closed: its missing packets are
+ * recorded lost and zero-filled, and it is correlated into the current dump.
+ * A complete oldest block closes at once.  Every blocks_per_dump blocks (the
+ * integration K = blocks_per_dump * block_samples) the dump is copied to a
+ * pinned host buffer, asynchronously.
+ *
+ * Packet format (Sec. 2.3, Fig. 3): XCORR_PACKET_HEADER_BYTES of header -- a
+ * 64-bit little-endian sequence number, a 32-bit little-endian F-engine id and
+ * 4 unused bytes -- then n_time_per_packet spectra one after another, each
+ * n_chan_per_packet channels x n_inputs_per_packet inputs of CI4 bytes
+ * ([t][channel][input]).  F-engine f sends inputs [f N_a, (f + 1) N_a); its
+ * sequence number counts its own packets: seq = time_block * n_groups +
+ * channel_group with n_groups = n_channels / n_chan_per_packet, time_block
+ * covering samples [time_block N_t, (time_block + 1) N_t).  Block b holds
+ * samples [b * block_samples, (b + 1) * block_samples).
+ */
+#define XCORR_PACKET_HEADER_BYTES 16
+
+typedef struct {
+    int n_time_per_packet;     /* N_t, >= 1                                                  */
+    int n_chan_per_packet;     /* divides the plan's n_channels                              */
+    int n_inputs_per_packet;   /* N_a: a multiple of 16 that divides n_inputs                */
+    int block_samples;         /* a multiple of N_t, <= the plan's max_time_per_exec         */
+    int n_blocks;              /* blocks in the device ring, >= 2 (the paper's rings hold 4) */
+    int blocks_per_dump;       /* >= 1; K = blocks_per_dump * block_samples <= the plan's
+                                  exact integration bound                                    */
+    int64_t stack_threshold;   /* >= 1: held packets of later blocks that close the oldest   */
+    int64_t chunk_packets;     /* packets per pinned landing chunk, >= 1                     */
+    int n_chunks;              /* landing chunks, >= 2                                       */
+    int n_host_dumps;          /* pinned host dump buffers, >= 1                             */
+} xcorr_stream_config;
+
+/* Packet accounting, cumulative. */
+typedef struct {
+    int64_t packets;        /* headers seen                                         */
+    int64_t placed;         /* distinct packets placed in the ring                  */
+    int64_t duplicates;     /* a (seq, F-engine) already placed in an open block    */
+    int64_t late;           /* for a block already closed                           */
+    int64_t bad;            /* F-engine id out of range                             */
+    int64_t lost;           /* never received by the time their block closed        */
+    int64_t blocks_closed;
+} xcorr_packet_counters;
+
+/*
+ * Host-side packet tracking, the decision logic of the stream without the
+ * GPU (usable from a capture thread, and testable on any host).
+ * xcorr_tracker_feed reads n headers (packet k at packets + k * stride) and
+ * writes codes[k] = (ring slot << 40) | packet index within the block, or -1
+ * when the packet is dropped (duplicate, late, bad).  The packet index of
+ * (time block tb in its block, channel group g, F-engine f) is
+ * (tb * n_groups + g) * n_fengines + f.  Each block event (an OPEN when a
+ * block takes a ring slot, a CLOSE when the oldest block is closed) is
+ * reported with the packet position in this call at which it takes effect.
+ * Processing stops early when max_events are reported; *n_done gives the
+ * packets consumed.  Errors: INVALID_ARG.
+ */
+typedef struct xcorr_tracker_s *xcorr_tracker;
+
+#define XCORR_EVENT_OPEN 1
+#define XCORR_EVENT_CLOSE 2
+
+typedef struct {
+    int kind;          /* XCORR_EVENT_OPEN or XCORR_EVENT_CLOSE                           */
+    int slot;          /* ring slot (block % n_blocks)                                    */
+    int64_t block;     /* block index                                                     */
+    int64_t position;  /* packets of this call before the event                           */
+    int64_t received;  /* CLOSE: distinct packets placed in the block                     */
+    int64_t lost;      /* CLOSE: packets of the block never received                      */
+} xcorr_block_event;
+
+xcorr_status xcorr_tracker_create(xcorr_tracker *out, const xcorr_stream_config *cfg, int n_inputs,
+                                  int n_channels);
+xcorr_status xcorr_tracker_feed(xcorr_tracker tr, const void *packets, int64_t stride, int64_t n,
+                                int64_t *codes, xcorr_block_event *events, int max_events,
+                                int *n_events, int64_t *n_done);
+/* Close every open block (end of stream).  Same event rules. */
+xcorr_status xcorr_tracker_finish(xcorr_tracker tr, xcorr_block_event *events, int max_events,
+                                  int *n_events);
+xcorr_status xcorr_tracker_counters(xcorr_tracker tr, xcorr_packet_counters *out);
+xcorr_status xcorr_tracker_destroy(xcorr_tracker tr);
+
+/*
+ * Cut CI4 samples [n_time][n_channels][n_inputs] (host, n_time a multiple of
+ * N_t) into packets in the order an F-engine array sends them: for each time
+ * block, each channel group, each F-engine.  Time block tb of the samples is
+ * time block first_time_block + tb of the stream.  Writes
+ * (n_time / N_t) * n_groups * n_fengines packets of 16 + N_t * N_ch * N_a
+ * bytes to `packets` (host).  Errors: INVALID_ARG (sizes, capacity).
+ */
+xcorr_status xcorr_packetize(const void *samples, int n_time, int n_channels, int n_inputs,
+                             const xcorr_stream_config *cfg, int64_t first_time_block,
+                             void *packets, int64_t capacity_packets, int64_t *n_packets);
+
+typedef struct xcorr_stream_s *xcorr_stream;
+
+typedef struct {
+    int64_t index;         /* dump number: block / blocks_per_dump                          */
+    int64_t n_samples;     /* samples integrated (blocks correlated x block_samples)        */
+    int64_t lost_packets;  /* zero-filled packets in this dump's blocks                     */
+    double latency_ms;     /* host time from closing the dump's last block to its copy
+                              being in host memory                                          */
+    const void *data;      /* pinned host copy, int32 [C][P][2], valid until n_host_dumps
+                              later dumps with data are issued; NULL when n_samples == 0
+                              or when that has already happened                            */
+} xcorr_dump_record;
+
+/*
+ * Create a stream over a CI4 plan (which it drives; do not execute the plan
+ * meanwhile).  The stream's device memory (ring, landing chunks, two dump
+ * buffers) plus the plan's must fit the plan's hbm_budget_bytes when that is
+ * nonzero.  Errors: INVALID_ARG, UNSUPPORTED (not CI4), BUDGET, OOM, CUDA.
+ */
+xcorr_status xcorr_stream_create(xcorr_stream *out, xcorr_plan plan, const xcorr_stream_config *cfg);
+
+/* The next landing chunk to fill with up to *capacity_packets packets (pinned
+ * host memory owned by the stream); waits until its previous contents reached
+ * the device.  Errors: INVALID_ARG, CUDA. */
+xcorr_status xcorr_stream_acquire(xcorr_stream s, void **chunk, int64_t *capacity_packets);
+
+/* Hand over the first n_packets of the acquired chunk: headers are tracked on
+ * the host, the chunk goes to the device and is scattered; closed blocks are
+ * correlated and finished dumps copied out, all asynchronously.
+ * Errors: INVALID_ARG, CUDA, DEVICE. */
+xcorr_status xcorr_stream_commit(xcorr_stream s, int64_t n_packets);
+
+/* End of stream: close every open block and issue the last (partial) dump. */
+xcorr_status xcorr_stream_flush(xcorr_stream s);
+
+/* Dumps issued so far, and the packet counters. */
+xcorr_status xcorr_stream_counters(xcorr_stream s, xcorr_packet_counters *counters,
+                                   int64_t *dumps_issued);
+
+/* Wait up to timeout_ms for the k-th dump issued (0-based) to reach host
+ * memory.  Errors: INVALID_ARG (k not issued yet), CUDA (timeout: the
+ * stream's copies did not finish), DEVICE. */
+xcorr_status xcorr_stream_wait_dump(xcorr_stream s, int64_t k, int timeout_ms, xcorr_dump_record *rec);
+
+/* Synchronise the stream's work and free it (not the plan).  NULL is a no-op. */
+xcorr_status xcorr_stream_destroy(xcorr_stream s);
+
 /* Synchronise the device, free the plan's memory and the plan.  NULL is a no-op. */
 xcorr_status xcorr_destroy(xcorr_plan plan);
 

@@ -48,13 +48,13 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     """Compile every translation unit and link the library; returns its path."""
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
-    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     headers = _headers()
     flags = FLAGS + (extra_flags or [])
     objs = []
     jobs = []
     for src in sources:
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(OUT_DIR, os.path.splitext(os.path.basename(src))[0] + ".o")
         objs.append(obj)
         if _stale(obj, [src] + headers):
             jobs.append([nvcc, *ARCH, *flags, "-c", src, "-o", obj])

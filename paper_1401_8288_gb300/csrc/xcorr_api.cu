@@ -100,11 +100,11 @@ int tensor_groups(xcorr_plan plan) {
   return g < 1 ? 1 : static_cast<int>(g);
 }
 
-// The 4-bit tensor path can unpack on chip: inputs a multiple of 16 (TMA row
-// strides), a 16-byte aligned pointer and one exact block per tile pair.
-bool fused_applies(xcorr_plan plan, const void* d_in, int n_time) {
+// The 4-bit tensor path can unpack on chip: inputs a multiple of 16 and a
+// 16-byte aligned pointer (the decoders read whole 16-sample chunks).
+bool fused_applies(xcorr_plan plan, const void* d_in) {
   return plan->cfg.fmt == XCORR_IN_CI4 && !plan->tune_unfused && plan->n_inputs % 16 == 0 &&
-         reinterpret_cast<uintptr_t>(d_in) % 16 == 0 && n_time <= xc::kTcWindowCI4;
+         reinterpret_cast<uintptr_t>(d_in) % 16 == 0;
 }
 
 // Unpack channels [c0, c0 + nc) of the input into the plan's planes.
@@ -136,21 +136,12 @@ xcorr_status run_execute(xcorr_plan plan, const void* d_in, int n_time, void* ta
     ev = plan->prof_events + xc::kProfileEvents * slot;
     if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return cuda_fail(e, "profile event");
   }
-  if (plan->engine == XCORR_ENGINE_TENSOR && fused_applies(plan, d_in, n_time)) {
-    // 4-bit input with the unpack on chip: one launch on the caller's stream
-    const int variant = plan->tune_variant;
-    if (plan->raw_in != d_in || plan->raw_ntime != n_time || plan->raw_variant != variant) {
-      std::string err;
-      if (!xc::encode_raw_ci4_tmap(&plan->raw_tmap, d_in, N, C, n_time, xc::fused_stage_samples(variant), &err))
-        return fail(XCORR_ERR_CUDA, err);
-      plan->raw_in = d_in;
-      plan->raw_ntime = n_time;
-      plan->raw_variant = variant;
-    }
+  if (plan->engine == XCORR_ENGINE_TENSOR && fused_applies(plan, d_in)) {
+    // 4-bit input with the unpack on chip: one launch per exact block, on the caller's stream
     if (ev && ((e = cudaEventRecord(ev[1], s)) != cudaSuccess || (e = cudaEventRecord(ev[2], s)) != cudaSuccess))
       return cuda_fail(e, "profile event");
-    e = xc::launch_xcorr_tc_fused_ci4(&plan->raw_tmap, variant, n_time, C, N, static_cast<int2*>(target),
-                                      !target_fresh, plan->status, plan->num_sms, s);
+    e = xc::launch_xcorr_tc_fused_ci4(static_cast<const uint8_t*>(d_in), plan->tune_variant, n_time, C, N,
+                                      static_cast<int2*>(target), !target_fresh, plan->status, plan->num_sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "fused X kernel launch");
     if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return cuda_fail(e, "profile event");
     if (ev) plan->prof_ngroups[plan->prof_count % plan->prof_cap] = 1;
@@ -247,6 +238,18 @@ xcorr_status run_execute(xcorr_plan plan, const void* d_in, int n_time, void* ta
 
 namespace xc {
 xcorr_status set_error(xcorr_status st, const std::string& msg) { return fail(st, msg); }
+xcorr_status plan_check(xcorr_plan plan) { return plan_ok(plan); }
+xcorr_status execute_into(xcorr_plan plan, const void* d_in, int n_time, void* target, bool target_fresh,
+                          cudaStream_t s) {
+  return run_execute(plan, d_in, n_time, target, target_fresh, s);
+}
+xcorr_status read_device_status(xcorr_plan plan) {
+  int code = 0;
+  cudaError_t e = cudaMemcpy(&code, plan->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (code) plan->sticky = code;
+  return plan_ok(plan);
+}
 }  // namespace xc
 
 extern "C" {
@@ -461,8 +464,10 @@ xcorr_status xcorr_plan_query(xcorr_plan plan, xcorr_plan_info* info) {
   info->device_bytes = plan->device_bytes;
   info->output_bytes = (size_t)plan->cfg.n_channels * plan->n_pairs * 8;
   const bool fused = plan->engine == XCORR_ENGINE_TENSOR && plan->cfg.fmt == XCORR_IN_CI4 && !plan->tune_unfused &&
-                     plan->n_inputs % 16 == 0 && plan->cfg.max_time_per_exec <= xc::kTcWindowCI4;
-  info->kernels_per_execute = fused ? 1 : plan->engine == XCORR_ENGINE_TENSOR ? 2 * tensor_groups(plan) : 1;
+                     plan->n_inputs % 16 == 0;
+  info->kernels_per_execute = fused ? xc::fused_launches(plan->cfg.max_time_per_exec)
+                              : plan->engine == XCORR_ENGINE_TENSOR ? 2 * tensor_groups(plan)
+                                                                     : 1;
   info->tuning.stage_variant = plan->tune_variant;
   info->tuning.groups = fused ? 1 : tensor_groups(plan);
   info->tuning.x_streams = plan->tune_x_streams;
@@ -513,7 +518,7 @@ xcorr_status xcorr_autotune(xcorr_plan plan, const void* d_in, int n_time, void*
   // candidates: the fused 4-bit kernel (3 stage shapes) where it applies, then
   // every planes-based shape
   plan->tune_unfused = 0;
-  const bool fused_ok = fused_applies(plan, d_in, n_time);
+  const bool fused_ok = fused_applies(plan, d_in);
   for (int uf = fused_ok ? 0 : 1; uf <= 1 && st == XCORR_OK; ++uf)
   for (int v = 0; v < xc::kTcVariants && st == XCORR_OK; ++v) {
     for (int gi = 0; gi < 4 && st == XCORR_OK; ++gi) {

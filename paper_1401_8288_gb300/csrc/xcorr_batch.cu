@@ -214,9 +214,10 @@ xcorr_status xcorr_batch_execute(xcorr_batch b, const void* const* d_ins, void* 
 
 xcorr_status xcorr_batch_capture(xcorr_batch b, const void* const* d_ins, void* const* d_outs, void* stream) {
   if (!b || !d_ins || !d_outs) return bfail(XCORR_ERR_INVALID_ARG, "batch, d_ins and d_outs must not be NULL");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSetDevice(b->device);
   if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  // (recording only: the graph runs later on whatever stream replays it)
+  cudaStreamSynchronize(static_cast<cudaStream_t>(stream));  // earlier launches may still read the tables
   xcorr_status st = build_tables(b, d_outs);
   if (st != XCORR_OK) return st;
   if (b->graph_exec) {
@@ -243,7 +244,6 @@ xcorr_status xcorr_batch_capture(xcorr_batch b, const void* const* d_ins, void* 
   cudaStreamDestroy(cap);
   if (st != XCORR_OK) return st;
   if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  (void)s;
   return XCORR_OK;
 }
 

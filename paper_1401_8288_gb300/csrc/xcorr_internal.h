@@ -27,6 +27,9 @@ constexpr int64_t kMaxIntegrationCI8 = (INT64_C(2147483647)) / 32768;  // 65,535
 // 64, 48, 32 for BF16).
 constexpr int kTcWindowCI4 = 130944;
 constexpr int kTcWindowBF16 = 384;
+// Offset-binary 4-bit operands u = t + 8 in [0, 15]: |sum_t (u_re u_re' + u_im u_im')| <= 450 T
+// stays below 2^24 for T <= 37,282; rounded down to a multiple of 384 (every stage height).
+constexpr int kFusedWindowCI4 = 37248;
 constexpr int kTcVariants = 3;  // stage shapes: 64 KB x 3, 48 KB x 4, 32 KB x 6
 constexpr int64_t kMaxIntegrationCF32 = INT64_C(16777216);  // FP32 per dump, widen beyond
 
@@ -71,9 +74,6 @@ struct xcorr_plan_s {
   int tune_x_streams = 2;      // X launches alternate over 1 or 2 streams
   int tune_unfused = 0;        // 4-bit input: 1 = always through planes, 0 = fuse the unpack when possible
 
-  CUtensorMap raw_tmap{};      // fused 4-bit path: the caller's input, for raw_* below
-  const void* raw_in = nullptr;
-  int raw_ntime = -1, raw_variant = -1;
 
   CUtensorMap tmap{};          // planes, for tmap_ntime / tmap_variant
   int tmap_ntime = -1;
@@ -147,6 +147,14 @@ int cuda_core_ksplit(int n_time, int n_chan, int n_inputs, int num_sms);
 
 // Record the calling thread's error message (read by xcorr_last_error) and return st.
 xcorr_status set_error(xcorr_status st, const std::string& msg);
+// For the library's other front ends (streams): the plan checks of every call,
+// one execute of n_time samples into `target` (store when target_fresh, else
+// add; the plan's own accumulator is untouched unless it is the target), and
+// a read of the device status word (DEVICE if a kernel gave up a wait).
+xcorr_status plan_check(xcorr_plan plan);
+xcorr_status execute_into(xcorr_plan plan, const void* d_in, int n_time, void* target, bool target_fresh,
+                          cudaStream_t s);
+xcorr_status read_device_status(xcorr_plan plan);
 
 cudaError_t launch_fold_wide_i64(const int2* acc, int64_t* out, int64_t n_pairs_total,
                                  cudaStream_t stream);
@@ -156,13 +164,17 @@ cudaError_t launch_fold_wide_i64(const int2* acc, int64_t* out, int64_t n_pairs_
 bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inputs, int ni_pad,
                        int n_time, int max_time, int n_planes_total, int box_t, std::string* err);
 
-// Tensor map over the caller's CI4 input [t][c][i] (needs n_inputs % 16 == 0 and
-// a 16-byte aligned pointer): boxes of 128 inputs x 1 channel x box_t samples.
+
+// Tensor map over the caller's CI4 input [t][c][i] (n_inputs % 16 == 0, 16-byte
+// aligned pointer): boxes of 128 inputs x 1 channel x box_t samples, 128-byte
+// swizzle (the fused kernel's raw tiles, and its L2 prefetches).
 bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int n_time, int box_t,
                          std::string* err);
-// The fused 4-bit X kernel (unpack on chip); n_time <= kTcWindowCI4.
+// The fused 4-bit X kernel (unpack on chip, offset-binary operands): one
+// launch per kFusedWindowCI4 samples; n_inputs % 16 == 0, `in` 16-byte aligned.
 int fused_stage_samples(int variant);
-cudaError_t launch_xcorr_tc_fused_ci4(const CUtensorMap* raw_map, int variant, int n_time, int n_chan, int n_inputs,
+int fused_launches(int n_time);
+cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int variant, int n_time, int n_chan, int n_inputs,
                                       int2* out, bool accumulate, int* status, int num_sms, cudaStream_t stream);
 
 // int8 (re, im) samples -> two BF16 planes [c][2][t][ni_pad] (exact).

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int blk = 0; blk < n_blocks; ++blk, ++g) {
         const int buf = g & 1;
         const uint32_t use = static_cast<uint32_t>(g >> 1);
-        if (!mbar_wait(&tfull[buf], use & 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL)) {
+        if (!mbar_wait_warp(&tfull[buf], use & 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL)) {
           ok = false;
           break;
         }

@@ -1,26 +1,34 @@
 // xcorr_tc_fused.cu -- the 4-bit X-stage with the unpack fused into the
 // tensor-core kernel.
 //
-// Same computation as xcorr_tc.cu for 4+4-bit input (per channel, the packed
-// lower triangle of V = sum_t x_t x_t^H; Sec. 1, Sec. 2.1, Eq. 1), but no
-// E4M3 planes are written to or read from HBM: TMA brings the raw CI4 bytes
-// of a 128-input x KT-sample tile straight from the caller's [t][c][i] input
-// (box: 128 inputs x 1 channel x KT samples), which lands in shared memory in
-// exactly the MN-major 128-byte-swizzled layout the MMA reads.  Eight decoder
-// warps turn each raw byte into its E4M3 real and imaginary codes at the same
-// offset of two operand tiles (Sec. 2.4's unpack, done on chip), and the MMA
-// thread issues the same three MMAs per 32-sample step into [Re | -Im].  HBM
-// traffic per step falls from input + 2 x planes written + planes read + output
-// to input + output.
+// Same result as xcorr_tc.cu for 4+4-bit input (per channel, the packed lower
+// triangle of V = sum_t x_t x_t^H; Sec. 1, Sec. 2.1, Eq. 1), but no E4M3
+// planes go through HBM: TMA brings the caller's raw [t][c][i] bytes of a
+// 128-input x KT-sample tile into a shared-memory ring (box 128 inputs x 1
+// channel x KT samples, 128-byte swizzle), and eight decoder warps turn each
+// raw byte into its real and imaginary E4M3 codes at the same offset of two
+// operand tiles -- the MN-major 128-byte-swizzled layout the MMA reads (Sec.
+// 2.4's unpack, done on chip).
 //
-// Warp roles (448 threads, one CTA per SM): warps 0-3 drain TMEM (one tile row
-// per thread) through a shared-memory transpose; warps 4-11 decode; warp 12
-// is the TMA producer; warp 13 allocates TMEM and issues the MMAs.  Rings:
-// RAW stages of raw tiles (I, J) and DEC stages of decoded tiles (Xr_I, Xi_I,
-// Xr_J, Xi_J).  One drained block per tile pair: the caller uses this kernel
-// only while n_time <= 130,944, where every FP32 partial sum is an exact
-// integer below 2^24.  Every wait is bounded (sm103_ptx.cuh).
-#include "ci4_decode.cuh"
+// Offset-binary operands.  A 4-bit two's-complement code t in [-8, 7] becomes
+// u = t + 8 in [0, 15] by flipping its top bit, and the byte u read as E4M3 is
+// exactly u * 2^-9 (codes 0..7 are subnormals m * 2^-9, codes 8..15 are
+// (8 + m) * 2^-9).  So the decode is one XOR and a mask per four samples, and
+// the MMAs produce sums of u_a u_b.  The true products follow from
+//   sum (u_a - 8)(u_b - 8) = sum u_a u_b - 8 S_a - 8 S_b + 64 T,
+// which needs the per-input sums S = sum_t u over the block: the decoders
+// accumulate them in byte lanes as they go, and the epilogue applies
+//   Re V_ab = Re' - 8 (P_a + P_b) + 128 T,   P = S_re + S_im,
+//   Im V_ab = Im' - 8 Q_a + 8 Q_b,           Q = S_im - S_re.
+// Every partial sum of u_a u_b is an integer multiple of 2^-18 below 2^6
+// (|Re'| <= 450 T), exact in the FP32 accumulator for T <= 37,282; a launch
+// covers at most 37,248 samples and longer integrations add launches.
+//
+// Warp roles (448 threads, one CTA per SM): warps 0-3 drain TMEM (one tile
+// row per thread) through a shared-memory transpose; warps 4-11 decode and
+// sum; warp 12 is the TMA producer (and prefetches into L2 further ahead);
+// warp 13 allocates TMEM and issues the three MMAs per 32-sample step into
+// [Re | -Im] (double-buffered).  Every wait is bounded (sm103_ptx.cuh).
 #include "sm103_ptx.cuh"
 #include "xcorr_internal.h"
 
@@ -39,23 +47,33 @@ constexpr int kPitch = kChunk + 1;
 constexpr int kAccCols = 256;  // [Re | -Im]
 constexpr uint32_t kTmemCols = 512;
 constexpr int kStagingBytes = kEpiWarps * 32 * kPitch * 8;
-constexpr int kBarrierBytes = 512;
+constexpr int kSumsBytes = 2 * 2 * kBlk * 8;            // [TMEM buffer][I, J][input] (P, Q)
+constexpr int kScratchBytes = kDecWarps * 8 * 16 * 8;   // [decoder warp][chunk][input] (P, Q)
+constexpr int kBarrierBytes = 256;
+constexpr uint32_t kNibbleTop = 0x88888888u;            // t -> t + 8 on every nibble
+constexpr uint32_t kLowNibbles = 0x0F0F0F0Fu;
+constexpr int kPrefetchSamples = 512;                   // L2 prefetch distance along time
 
 template <int KT, int RAW, int DEC>
 struct FGeom {
-  static constexpr int kTile = KT * 128;        // one 128-input tile, raw or decoded
-  static constexpr int kRawStage = 2 * kTile;   // raw I, raw J
-  static constexpr int kDecStage = 4 * kTile;   // Xr_I, Xi_I, Xr_J, Xi_J
-  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kDecStage + kStagingBytes + kBarrierBytes;
-  static constexpr int kSteps = KT / 32;        // MMA steps (32 samples) per stage
+  static constexpr int kTile = KT * kBlk;        // one 128-input x KT-sample tile, raw or decoded
+  static constexpr int kRawStage = 2 * kTile;    // raw I, raw J
+  static constexpr int kDecStage = 4 * kTile;    // Xr_I, Xi_I, Xr_J, Xi_J
+  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kDecStage + kStagingBytes + kSumsBytes +
+                               kScratchBytes + kBarrierBytes;
+  static constexpr int kSteps = KT / 32;         // MMA steps (32 samples) per stage
   static_assert(KT % 32 == 0, "stage must hold whole MMA steps");
   static_assert(kSmem <= 232448, "shared memory budget");
 };
 
 struct FParams {
-  int n_chan, n_inputs, n_tile_pairs, n_kt;
+  const uint8_t* in;   // [t][c][i] CI4 bytes
+  int64_t row_stride;  // bytes from one sample to the next (n_chan * n_inputs)
+  int n_chan, n_inputs, n_tile_pairs;
+  int t0, t_end;       // samples [t0, t_end) of this launch
+  int n_kt;            // stages per tile pair
   int64_t n_pairs;
-  int accumulate;  // add into out (else store)
+  int accumulate;      // add into out (else store)
   int2* out;
   int* status;
 };
@@ -68,6 +86,128 @@ __device__ __forceinline__ void tile_pair(int p, int& I, int& J) {
   J = p - i * (i + 1) / 2;
 }
 
+
+// L2 prefetch of one TMA box (no shared memory, nothing to wait for).
+__device__ __forceinline__ void tma_prefetch_3d(const void* tmap, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                   reinterpret_cast<uint64_t>(tmap)),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+
+// A tile pair of the CTA's item list.
+struct Item {
+  int c, I, J;
+  bool diag, valid;
+};
+
+__device__ __forceinline__ Item item_at(const FParams& p, int item, int n_items) {
+  Item it{};
+  it.valid = item < n_items;
+  if (it.valid) {
+    it.c = item / p.n_tile_pairs;
+    tile_pair(item - it.c * p.n_tile_pairs, it.I, it.J);
+    it.diag = it.I == it.J;
+  }
+  return it;
+}
+
+// L2 prefetch of stage s of an item: one box per tile (128 inputs x KT samples).
+template <int KT>
+__device__ __forceinline__ void prefetch_stage(const CUtensorMap* raw_map, const FParams& p, const Item& it, int s) {
+  if (!it.valid || s >= p.n_kt) return;
+  const int t = p.t0 + s * KT;
+  tma_prefetch_3d(raw_map, it.I * kBlk, it.c, t);
+  if (!it.diag) tma_prefetch_3d(raw_map, it.J * kBlk, it.c, t);
+}
+
+// The decoder warps' own barrier (id 1), and its OR-reduction form.
+__device__ __forceinline__ void dec_bar_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool dec_bar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, 1, 256, q;\nselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(v))
+      : "memory");
+  return r != 0;
+}
+
+// Four CI4 bytes -> four offset E4M3 real codes and four imaginary codes.
+__device__ __forceinline__ void offset_codes(uint32_t w, uint32_t& re, uint32_t& im) {
+  const uint32_t u = w ^ kNibbleTop;
+  im = u & kLowNibbles;
+  re = (u >> 4) & kLowNibbles;
+}
+
+// One decoder thread's share of one tile pair: a fixed 16-input chunk L of one
+// tile and rows phase, phase + KT/R, ...; R rows per stage.  A raw chunk sits
+// at the same swizzled offset as its decoded chunks (TMA and the MMA use the
+// same 128-byte swizzle), so the thread reads and writes offset `pos` of each
+// row.  Returns the chunk's per-input sums in 16-bit lanes (word e/2, half
+// e%2 holds input e); false if a wait gave up.
+template <int KT, int RAW, int DEC, int R>
+__device__ __forceinline__ bool decode_item(const FParams& p, const uint8_t* raw, uint8_t* dec, uint64_t* raw_full,
+                                            uint64_t* raw_empty, uint64_t* dec_full, uint64_t* dec_empty,
+                                            volatile int* abort_flag, int& r, uint32_t& rph, int& d, uint32_t& dph,
+                                            int slot, int tp, int lane, uint32_t (&s_re)[8], uint32_t (&s_im)[8]) {
+  using G = FGeom<KT, RAW, DEC>;
+  constexpr int kStep = KT / R;  // 16 or 32: a multiple of 8, so every row of the thread has the same swizzle
+  const int L = tp & 7, phase = tp >> 3;
+  const int pos = (L ^ (phase & 7)) << 4;  // 128-byte swizzle: chunk L of row r sits at chunk L ^ (r % 8)
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s_re[q] = s_im[q] = 0u;
+  for (int tb = 0; tb < p.n_kt; ++tb) {
+    if (!mbar_wait_warp(&raw_full[r], rph, abort_flag, p.status, DEV_TIMEOUT_FULL) ||
+        !mbar_wait_warp(&dec_empty[d], dph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY))
+      return false;
+    const uint8_t* src = raw + r * G::kRawStage + slot * G::kTile + pos;
+    uint8_t* re_t = dec + d * G::kDecStage + (2 * slot) * G::kTile + pos;
+    uint8_t* im_t = re_t + G::kTile;
+    uint4 v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = *reinterpret_cast<const uint4*>(src + (phase + k * kStep) * 128);
+    uint32_t a_re[4] = {0u, 0u, 0u, 0u}, a_im[4] = {0u, 0u, 0u, 0u};  // byte lanes: <= 15 * R <= 120
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      uint4 re, im;
+      offset_codes(v[k].x, re.x, im.x);
+      offset_codes(v[k].y, re.y, im.y);
+      offset_codes(v[k].z, re.z, im.z);
+      offset_codes(v[k].w, re.w, im.w);
+      a_re[0] += re.x, a_re[1] += re.y, a_re[2] += re.z, a_re[3] += re.w;
+      a_im[0] += im.x, a_im[1] += im.y, a_im[2] += im.z, a_im[3] += im.w;
+      const int off = (phase + k * kStep) * 128;
+      *reinterpret_cast<uint4*>(re_t + off) = re;
+      *reinterpret_cast<uint4*>(im_t + off) = im;
+    }
+    // widen to 16-bit lanes: inputs (4q, 4q+1) -> word 2q, (4q+2, 4q+3) -> word 2q+1
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      s_re[2 * q] += __byte_perm(a_re[q], 0u, 0x4140);
+      s_re[2 * q + 1] += __byte_perm(a_re[q], 0u, 0x4342);
+      s_im[2 * q] += __byte_perm(a_im[q], 0u, 0x4140);
+      s_im[2 * q + 1] += __byte_perm(a_im[q], 0u, 0x4342);
+    }
+    // the MMA reads the tiles through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&raw_empty[r]);
+      mbar_arrive(&dec_full[d]);
+    }
+    if (++r == RAW) {
+      r = 0;
+      rph ^= 1u;
+    }
+    if (++d == DEC) {
+      d = 0;
+      dph ^= 1u;
+    }
+  }
+  return true;
+}
+
 template <int KT, int RAW, int DEC>
 __global__ void __launch_bounds__(kThreads, 1)
     xcorr_tc_fused_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ FParams p) {
@@ -75,15 +215,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* raw = smem;
-  uint8_t* dec = smem + RAW * G::kRawStage;
+  uint8_t* dec = raw + RAW * G::kRawStage;
   int2* staging = reinterpret_cast<int2*>(dec + DEC * G::kDecStage);
-  uint64_t* raw_full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(staging) + kStagingBytes);
+  int2* sums = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(staging) + kStagingBytes);  // [2][2][128]
+  int2* scratch = sums + 2 * 2 * kBlk;                                                           // [8][8][16]
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(scratch + kDecWarps * 8 * 16);
   uint64_t* raw_empty = raw_full + RAW;
   uint64_t* dec_full = raw_empty + RAW;
   uint64_t* dec_empty = dec_full + DEC;
   uint64_t* tfull = dec_empty + DEC;
   uint64_t* tempty = tfull + 2;
-  uint64_t* mma_done = tempty + 2;
+  uint64_t* sfull = tempty + 2;
+  uint64_t* mma_done = sfull + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -100,6 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kEpiWarps);
+      mbar_init(&sfull[b], 1);
     }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
@@ -114,24 +258,31 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == kProducerWarp) {
     if (lane == 0) {
+      constexpr int kAhead = kPrefetchSamples / KT;  // L2 prefetch runs this many stages ahead of the loads
       prefetch_tmap(&raw_map);
+      {
+        const Item first = item_at(p, blockIdx.x, n_items);
+        for (int s = 0; s < kAhead; ++s) prefetch_stage<KT>(&raw_map, p, first, s);
+      }
       int r = 0;
       uint32_t ph = 0, filled = 0, fill_parity[RAW] = {};
       bool ok = true;
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-        const int c = item / p.n_tile_pairs;
-        int I, J;
-        tile_pair(item - c * p.n_tile_pairs, I, J);
-        const bool diag = (I == J);
+        const Item it = item_at(p, item, n_items);
         for (int tb = 0; tb < p.n_kt; ++tb) {
+          if (tb + kAhead < p.n_kt)
+            prefetch_stage<KT>(&raw_map, p, it, tb + kAhead);
+          else
+            prefetch_stage<KT>(&raw_map, p, item_at(p, item + gridDim.x, n_items), tb + kAhead - p.n_kt);
           if (!mbar_wait(&raw_empty[r], ph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
             ok = false;
             break;
           }
           uint8_t* st = raw + r * G::kRawStage;
-          mbar_expect_tx(&raw_full[r], (diag ? 1 : 2) * G::kTile);
-          tma_load_3d(st, &raw_map, &raw_full[r], I * kBlk, c, tb * KT);
-          if (!diag) tma_load_3d(st + G::kTile, &raw_map, &raw_full[r], J * kBlk, c, tb * KT);
+          const int t = p.t0 + tb * KT;
+          mbar_expect_tx(&raw_full[r], (it.diag ? 1 : 2) * G::kTile);
+          tma_load_3d(st, &raw_map, &raw_full[r], it.I * kBlk, it.c, t);
+          if (!it.diag) tma_load_3d(st + G::kTile, &raw_map, &raw_full[r], it.J * kBlk, it.c, t);
           fill_parity[r] = ph;
           filled |= 1u << r;
           if (++r == RAW) {
@@ -146,53 +297,57 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (filled & (1u << q)) mbar_wait(&raw_full[q], fill_parity[q], &never, p.status, DEV_TIMEOUT_DRAIN);
     }
   } else if (warp >= kDecWarp0 && warp < kDecWarp0 + kDecWarps) {
-    // Decoders: raw CI4 bytes -> E4M3 real / imaginary codes at the same offsets.
     const int tid = (warp - kDecWarp0) * 32 + lane;
-    int r = 0, d = 0;
+    const int dw = warp - kDecWarp0;
+    int r = 0, d = 0, g = 0;
     uint32_t rph = 0, dph = 0;
-    bool ok = true;
-    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-      const int c = item / p.n_tile_pairs;
-      int I, J;
-      tile_pair(item - c * p.n_tile_pairs, I, J);
-      const int total = (I == J ? 1 : 2) * (G::kTile / 16);  // 16-byte chunks this stage
-      for (int tb = 0; tb < p.n_kt; ++tb) {
-        if (!mbar_wait(&raw_full[r], rph, abort_flag, p.status, DEV_TIMEOUT_FULL) ||
-            !mbar_wait(&dec_empty[d], dph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
-          ok = false;
-          break;
-        }
-        const uint4* src = reinterpret_cast<const uint4*>(raw + r * G::kRawStage);
-        uint8_t* dst = dec + d * G::kDecStage;
-#pragma unroll 4
-        for (int q = tid; q < total; q += kDecWarps * 32) {
-          const int tile = q / (G::kTile / 16);
-          const int off = (q - tile * (G::kTile / 16)) * 16;
-          const uint4 v = src[q];
-          uint4 re, im;
-          ci4_to_e4m3(v.x, re.x, im.x);
-          ci4_to_e4m3(v.y, re.y, im.y);
-          ci4_to_e4m3(v.z, re.z, im.z);
-          ci4_to_e4m3(v.w, re.w, im.w);
-          *reinterpret_cast<uint4*>(dst + (2 * tile) * G::kTile + off) = re;
-          *reinterpret_cast<uint4*>(dst + (2 * tile + 1) * G::kTile + off) = im;
-        }
-        // the MMA reads the tiles through the async proxy
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&raw_empty[r]);
-          mbar_arrive(&dec_full[d]);
-        }
-        if (++r == RAW) {
-          r = 0;
-          rph ^= 1u;
-        }
-        if (++d == DEC) {
-          d = 0;
-          dph ^= 1u;
-        }
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
+      const Item cur = item_at(p, item, n_items);
+      const bool diag = cur.diag;
+      uint32_t s_re[8], s_im[8];
+      // off the diagonal, threads 0-127 take tile I and 128-255 tile J; on it, all take tile I
+      const bool ok_dec =
+          diag ? decode_item<KT, RAW, DEC, KT / 32>(p, raw, dec, raw_full, raw_empty, dec_full, dec_empty, abort_flag,
+                                                    r, rph, d, dph, 0, tid, lane, s_re, s_im)
+               : decode_item<KT, RAW, DEC, KT / 16>(p, raw, dec, raw_full, raw_empty, dec_full, dec_empty, abort_flag,
+                                                    r, rph, d, dph, tid >> 7, tid & 127, lane, s_re, s_im);
+      bool ok = ok_dec;
+      // per-input sums of this item: within the warp, lanes L, L+8, L+16, L+24 hold chunk L
+      int2 pq[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int sr = ok ? static_cast<int>((s_re[e >> 1] >> (16 * (e & 1))) & 0xFFFFu) : 0;
+        const int si = ok ? static_cast<int>((s_im[e >> 1] >> (16 * (e & 1))) & 0xFFFFu) : 0;
+        pq[e] = make_int2(sr + si, si - sr);
       }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        pq[e].x += __shfl_xor_sync(0xFFFFFFFFu, pq[e].x, 8);
+        pq[e].y += __shfl_xor_sync(0xFFFFFFFFu, pq[e].y, 8);
+        pq[e].x += __shfl_xor_sync(0xFFFFFFFFu, pq[e].x, 16);
+        pq[e].y += __shfl_xor_sync(0xFFFFFFFFu, pq[e].y, 16);
+      }
+      if (lane < 8) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) scratch[(dw * 8 + lane) * 16 + e] = pq[e];
+      }
+      dec_bar_sync();
+      const int buf = g & 1;
+      const uint32_t use = static_cast<uint32_t>(g >> 1);
+      if (ok) ok = mbar_wait(&tempty[buf], (use & 1u) ^ 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_EMPTY);
+      if (ok && (!diag || tid < 128)) {
+        const int slot = diag ? 0 : tid >> 7, e = tid & 127;
+        const int w0 = diag ? 0 : slot * 4, nw = diag ? 8 : 4;
+        int2 s = make_int2(0, 0);
+        for (int w = w0; w < w0 + nw; ++w) {
+          const int2 x = scratch[(w * 8 + (e >> 4)) * 16 + (e & 15)];
+          s.x += x.x;
+          s.y += x.y;
+        }
+        sums[(buf * 2 + slot) * kBlk + e] = s;
+      }
+      if (dec_bar_or(!ok || *abort_flag)) break;
+      if (tid == 0) mbar_arrive(&sfull[buf]);
     }
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
@@ -253,9 +408,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Epilogue: warp w drains TMEM lanes 32w .. 32w + 31 (tile rows), 16 columns at a time.
     int2* stage_rows = staging + warp * 32 * kPitch;
     const int half = lane >> 4, col = lane & 15;
+    const int t128 = 128 * p.n_kt * KT;  // 128 T over the padded block (padding decodes to u = 8 + 8i)
     int g = 0;
-    bool ok = true;
-    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x, ++g) {
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
       const int c = item / p.n_tile_pairs;
       int I, J;
       tile_pair(item - c * p.n_tile_pairs, I, J);
@@ -263,11 +418,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row0 = I * kBlk + warp * 32;
       const int buf = g & 1;
       const uint32_t use = static_cast<uint32_t>(g >> 1);
-      if (!mbar_wait(&tfull[buf], use & 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL)) {
-        ok = false;
+      if (!mbar_wait_warp(&tfull[buf], use & 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL) ||
+          !mbar_wait_warp(&sfull[buf], use & 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL))
         break;
-      }
       tc_fence_after();
+      const int2 rs = sums[(buf * 2) * kBlk + warp * 32 + lane];
+      const int2* cs = sums + (buf * 2 + (I == J ? 0 : 1)) * kBlk;
       const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + buf * kAccCols;
       for (int j0 = 0; j0 < kBlk; j0 += kChunk) {
         uint32_t re[16], nim[16];
@@ -277,9 +433,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int jfirst = J * kBlk + j0;
         if (jfirst > row0 + 31 || row0 >= p.n_inputs) continue;  // wholly above the diagonal or past the inputs
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
-          stage_rows[lane * kPitch + q] = make_int2(__float2int_rn(__uint_as_float(re[q])),
-                                                    -__float2int_rn(__uint_as_float(nim[q])));
+        for (int q = 0; q < 16; ++q) {
+          const int2 s = cs[j0 + q];
+          const int re_u = __float2int_rn(__uint_as_float(re[q]) * 262144.0f);  // sums of u_a u_b
+          const int nim_u = __float2int_rn(__uint_as_float(nim[q]) * 262144.0f);
+          stage_rows[lane * kPitch + q] = make_int2(re_u - 8 * (rs.x + s.x) + t128, -nim_u - 8 * rs.y + 8 * s.y);
+        }
         __syncwarp();
         // a half-warp writes 16 consecutive pairs of one row
         const int j = jfirst + col;
@@ -289,25 +448,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int i = row0 + 2 * r + half;
           if (i < p.n_inputs && j <= i) valid |= 1u << r;
         }
-        int2 old[16];
-        if (p.accumulate) {  // (continuing an integration: loads first, then adds)
-#pragma unroll 1
-          for (int r = 0; r < 16; ++r) {
-            const int i = row0 + 2 * r + half;
-            old[r] = (valid >> r) & 1u ? out_c[(int64_t)i * (i + 1) / 2 + j] : make_int2(0, 0);
-          }
-        }
+        // 8 rows at a time; when the integration continues, all 8 loads go out before the adds
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          if ((valid >> r) & 1u) {
-            const int rr = 2 * r + half;
-            const int i = row0 + rr;
-            int2 v = stage_rows[rr * kPitch + col];
-            if (p.accumulate) {
-              v.x += old[r].x;
-              v.y += old[r].y;
+        for (int h = 0; h < 2; ++h) {
+          int2 old[8];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int rh = 8 * h + r, i = row0 + 2 * rh + half;
+            old[r] = (p.accumulate && ((valid >> rh) & 1u)) ? out_c[(int64_t)i * (i + 1) / 2 + j] : make_int2(0, 0);
+          }
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int rh = 8 * h + r;
+            if ((valid >> rh) & 1u) {
+              const int rr = 2 * rh + half;
+              const int i = row0 + rr;
+              const int2 v = stage_rows[rr * kPitch + col];
+              out_c[(int64_t)i * (i + 1) / 2 + j] = make_int2(v.x + old[r].x, v.y + old[r].y);
             }
-            out_c[(int64_t)i * (i + 1) / 2 + j] = v;
           }
         }
         __syncwarp();
@@ -327,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int KT, int RAW, int DEC>
-cudaError_t launch_fused(const CUtensorMap* raw_map, const FParams& p, int grid, cudaStream_t stream) {
+cudaError_t launch_fused(const CUtensorMap& raw_map, const FParams& p, int grid, cudaStream_t stream) {
   using G = FGeom<KT, RAW, DEC>;
   auto kern = xcorr_tc_fused_kernel<KT, RAW, DEC>;
   static int attr_device = -1;
@@ -339,37 +497,53 @@ cudaError_t launch_fused(const CUtensorMap* raw_map, const FParams& p, int grid,
     if (e != cudaSuccess) return e;
     attr_device = dev;
   }
-  kern<<<grid, kThreads, G::kSmem, stream>>>(*raw_map, p);
+  kern<<<grid, kThreads, G::kSmem, stream>>>(raw_map, p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// Stage heights of the fused variants: 128 samples (2 raw + 2 decoded stages),
-// 96 (2 + 3), 64 (4 + 4).
+// Stage heights of the fused variants: 128 samples (2 raw + 2 decoded stages), 96 (2 + 3), 64 (4 + 4).
 int fused_stage_samples(int variant) { return variant == 0 ? 128 : variant == 1 ? 96 : 64; }
 
-cudaError_t launch_xcorr_tc_fused_ci4(const CUtensorMap* raw_map, int variant, int n_time, int n_chan, int n_inputs,
+int fused_launches(int n_time) { return n_time <= 0 ? 0 : (n_time + kFusedWindowCI4 - 1) / kFusedWindowCI4; }
+
+cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int variant, int n_time, int n_chan, int n_inputs,
                                       int2* out, bool accumulate, int* status, int num_sms, cudaStream_t stream) {
   const int nb = (n_inputs + kBlk - 1) / kBlk;
   const int kt = fused_stage_samples(variant);
+  if (n_time <= 0 || n_inputs % 16 != 0 || reinterpret_cast<uintptr_t>(in) % 16 != 0 ||
+      kFusedWindowCI4 % kt != 0)
+    return cudaErrorInvalidValue;
   FParams p{};
+  p.in = in;
+  p.row_stride = (int64_t)n_chan * n_inputs;
   p.n_chan = n_chan;
   p.n_inputs = n_inputs;
   p.n_tile_pairs = nb * (nb + 1) / 2;
-  p.n_kt = (n_time + kt - 1) / kt;
   p.n_pairs = (int64_t)n_inputs * (n_inputs + 1) / 2;
-  p.accumulate = accumulate ? 1 : 0;
   p.out = out;
   p.status = status;
-  if (n_time > kTcWindowCI4) return cudaErrorInvalidValue;  // one exact block per tile pair
   const int64_t items = (int64_t)n_chan * p.n_tile_pairs;
   const int grid = static_cast<int>(items < num_sms ? items : num_sms);
-  switch (variant) {
-    case 0: return launch_fused<128, 2, 2>(raw_map, p, grid, stream);
-    case 1: return launch_fused<96, 2, 3>(raw_map, p, grid, stream);
-    default: return launch_fused<64, 4, 4>(raw_map, p, grid, stream);
+  CUtensorMap raw_map;
+  if (!encode_raw_ci4_tmap(&raw_map, in, n_inputs, n_chan, n_time, kt, nullptr)) return cudaErrorInvalidValue;
+  // one exactly-summed block per launch; later blocks add into the first
+  for (int t0 = 0; t0 < n_time; t0 += kFusedWindowCI4) {
+    const int len = n_time - t0 < kFusedWindowCI4 ? n_time - t0 : kFusedWindowCI4;
+    p.t0 = t0;
+    p.t_end = t0 + len;
+    p.n_kt = (len + kt - 1) / kt;
+    p.accumulate = (accumulate || t0 > 0) ? 1 : 0;
+    cudaError_t e;
+    switch (variant) {
+      case 0: e = launch_fused<128, 2, 2>(raw_map, p, grid, stream); break;
+      case 1: e = launch_fused<96, 2, 3>(raw_map, p, grid, stream); break;
+      default: e = launch_fused<64, 4, 4>(raw_map, p, grid, stream); break;
+    }
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
 }  // namespace xc

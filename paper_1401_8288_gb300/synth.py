@@ -197,3 +197,23 @@ def uniform_ci4_torch(n_time: int, n_chan: int, n_sta: int, seed: int, device: s
     re = torch.randint(lo, hi + 1, shape, generator=g, device=device, dtype=torch.int16)
     im = torch.randint(lo, hi + 1, shape, generator=g, device=device, dtype=torch.int16)
     return (((re & 0xF) << 4) | (im & 0xF)).to(torch.uint8)
+
+
+def gaussian_ci4_torch(n_time: int, n_chan: int, n_sta: int, seed: int, sigma: float = 2.5,
+                       device: str = "cuda"):
+    """Complex Gaussian noise, sigma levels per component, rounded and clipped
+    to [-7, 7], drawn on the device (torch Philox): the requantised channel
+    data of an F-engine for large streaming inputs.  uint8 [t][c][s][2]."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    shape = (n_time, n_chan, n_sta, 2)
+    out = torch.empty(shape, dtype=torch.uint8, device=device)
+    step = max(1, (1 << 28) // (n_chan * n_sta * 2))  # bounded temporaries
+    for t0 in range(0, n_time, step):
+        t1 = min(n_time, t0 + step)
+        sub = (t1 - t0, n_chan, n_sta, 2)
+        re = torch.randn(sub, generator=g, device=device).mul_(sigma).round_().clamp_(-7, 7).to(torch.int16)
+        im = torch.randn(sub, generator=g, device=device).mul_(sigma).round_().clamp_(-7, 7).to(torch.int16)
+        out[t0:t1] = (((re & 0xF) << 4) | (im & 0xF)).to(torch.uint8)
+    return out

@@ -32,7 +32,13 @@ EXPORTS = ("xcorr_plan_create", "xcorr_execute", "xcorr_dump", "xcorr_sync", "xc
            "xcorr_profile_read", "xcorr_measure_peak", "xcorr_correlate_ci4_noalloc",
            "xcorr_execute_dump", "xcorr_plan_set_tuning", "xcorr_autotune", "xcorr_batch_create",
            "xcorr_batch_set_variant", "xcorr_batch_execute", "xcorr_batch_capture",
-           "xcorr_batch_replay", "xcorr_batch_sync", "xcorr_batch_destroy")
+           "xcorr_batch_replay", "xcorr_batch_sync", "xcorr_batch_destroy", "xcorr_tracker_create",
+           "xcorr_tracker_feed", "xcorr_tracker_finish", "xcorr_tracker_counters",
+           "xcorr_tracker_destroy", "xcorr_packetize", "xcorr_stream_create", "xcorr_stream_acquire",
+           "xcorr_stream_commit", "xcorr_stream_flush", "xcorr_stream_counters",
+           "xcorr_stream_wait_dump", "xcorr_stream_destroy")
+XCORR_PACKET_HEADER_BYTES = 16
+XCORR_EVENT_OPEN, XCORR_EVENT_CLOSE = 1, 2
 PEAK_KINDS = {"tc_e4m3": 0, "tc_bf16": 1, "mma_sync_s8": 2, "dp4a": 3}
 
 
@@ -60,6 +66,31 @@ class xcorr_plan_info(ctypes.Structure):
                 ("samples_integrated", ctypes.c_int64), ("max_integration", ctypes.c_int64),
                 ("device_bytes", ctypes.c_size_t), ("output_bytes", ctypes.c_size_t),
                 ("kernels_per_execute", ctypes.c_int), ("tuning", xcorr_tuning)]
+
+
+class xcorr_stream_config(ctypes.Structure):
+    _fields_ = [("n_time_per_packet", ctypes.c_int), ("n_chan_per_packet", ctypes.c_int),
+                ("n_inputs_per_packet", ctypes.c_int), ("block_samples", ctypes.c_int),
+                ("n_blocks", ctypes.c_int), ("blocks_per_dump", ctypes.c_int),
+                ("stack_threshold", ctypes.c_int64), ("chunk_packets", ctypes.c_int64),
+                ("n_chunks", ctypes.c_int), ("n_host_dumps", ctypes.c_int)]
+
+
+class xcorr_packet_counters(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in
+                ("packets", "placed", "duplicates", "late", "bad", "lost", "blocks_closed")]
+
+
+class xcorr_block_event(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("slot", ctypes.c_int), ("block", ctypes.c_int64),
+                ("position", ctypes.c_int64), ("received", ctypes.c_int64),
+                ("lost", ctypes.c_int64)]
+
+
+class xcorr_dump_record(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_int64), ("n_samples", ctypes.c_int64),
+                ("lost_packets", ctypes.c_int64), ("latency_ms", ctypes.c_double),
+                ("data", ctypes.c_void_p)]
 
 
 _lib = None
@@ -103,6 +134,24 @@ def load():
                 "xcorr_batch_destroy": [vp],
                 "xcorr_autotune": [vp, vp, i, vp, ctypes.POINTER(xcorr_tuning),
                                    ctypes.POINTER(ctypes.c_float)],
+                "xcorr_tracker_create": [ctypes.POINTER(vp), ctypes.POINTER(xcorr_stream_config), i,
+                                         i],
+                "xcorr_tracker_feed": [vp, vp, i64, i64, vp, ctypes.POINTER(xcorr_block_event), i,
+                                       ctypes.POINTER(i), ctypes.POINTER(i64)],
+                "xcorr_tracker_finish": [vp, ctypes.POINTER(xcorr_block_event), i,
+                                         ctypes.POINTER(i)],
+                "xcorr_tracker_counters": [vp, ctypes.POINTER(xcorr_packet_counters)],
+                "xcorr_tracker_destroy": [vp],
+                "xcorr_packetize": [vp, i, i, i, ctypes.POINTER(xcorr_stream_config), i64, vp, i64,
+                                    ctypes.POINTER(i64)],
+                "xcorr_stream_create": [ctypes.POINTER(vp), vp, ctypes.POINTER(xcorr_stream_config)],
+                "xcorr_stream_acquire": [vp, ctypes.POINTER(vp), ctypes.POINTER(i64)],
+                "xcorr_stream_commit": [vp, i64],
+                "xcorr_stream_flush": [vp],
+                "xcorr_stream_counters": [vp, ctypes.POINTER(xcorr_packet_counters),
+                                          ctypes.POINTER(i64)],
+                "xcorr_stream_wait_dump": [vp, i64, i, ctypes.POINTER(xcorr_dump_record)],
+                "xcorr_stream_destroy": [vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -257,6 +306,166 @@ def xcorr_batch_sync(batch, stream: int = 0) -> None:
 
 def xcorr_batch_destroy(batch) -> None:
     _check(load().xcorr_batch_destroy(batch))
+
+
+# --------------------------------------------------------------- streaming --
+def stream_config(n_time_per_packet: int, n_chan_per_packet: int, n_inputs_per_packet: int,
+                  block_samples: int, n_blocks: int = 4, blocks_per_dump: int = 1,
+                  stack_threshold: int = 1 << 30, chunk_packets: int = 4096, n_chunks: int = 4,
+                  n_host_dumps: int = 2) -> xcorr_stream_config:
+    return xcorr_stream_config(n_time_per_packet, n_chan_per_packet, n_inputs_per_packet,
+                               block_samples, n_blocks, blocks_per_dump, stack_threshold,
+                               chunk_packets, n_chunks, n_host_dumps)
+
+
+def packet_bytes(cfg: xcorr_stream_config) -> int:
+    return (XCORR_PACKET_HEADER_BYTES
+            + cfg.n_time_per_packet * cfg.n_chan_per_packet * cfg.n_inputs_per_packet)
+
+
+def _counters_dict(c: xcorr_packet_counters) -> dict:
+    return {name: getattr(c, name) for name, _ in xcorr_packet_counters._fields_}
+
+
+def xcorr_packetize(samples, cfg: xcorr_stream_config, first_time_block: int = 0):
+    """CI4 samples uint8 [t][c][i] (host) -> packets uint8 [n][packet bytes], F-engine order."""
+    import numpy as np
+    x = np.ascontiguousarray(samples, dtype=np.uint8)
+    n_time, n_chan, n_in = x.shape[0], x.shape[1], int(np.prod(x.shape[2:]))
+    n_groups, n_feng = n_chan // cfg.n_chan_per_packet, n_in // cfg.n_inputs_per_packet
+    cap = (n_time // max(cfg.n_time_per_packet, 1)) * n_groups * n_feng
+    out = np.empty((cap, packet_bytes(cfg)), dtype=np.uint8)
+    n = ctypes.c_int64()
+    _check(load().xcorr_packetize(x.ctypes.data, n_time, n_chan, n_in, ctypes.byref(cfg),
+                                  first_time_block, out.ctypes.data, cap, ctypes.byref(n)))
+    return out[:n.value]
+
+
+class Tracker:
+    """Host-side packet tracking (no GPU): placement codes and block events."""
+
+    def __init__(self, cfg: xcorr_stream_config, n_inputs: int, n_channels: int,
+                 max_events: int = 1024):
+        self.cfg = cfg
+        self.handle = ctypes.c_void_p()
+        _check(load().xcorr_tracker_create(ctypes.byref(self.handle), ctypes.byref(cfg), n_inputs,
+                                           n_channels))
+        self._events = (xcorr_block_event * max_events)()
+        self._max = max_events
+
+    def _ev_list(self, n: int, offset: int = 0) -> list[dict]:
+        return [{"kind": e.kind, "slot": e.slot, "block": e.block, "position": e.position + offset,
+                 "received": e.received, "lost": e.lost} for e in self._events[:n]]
+
+    def feed(self, packets):
+        """packets: uint8 [n][packet bytes]; returns (codes int64 [n], events)."""
+        import numpy as np
+        pk = np.ascontiguousarray(packets, dtype=np.uint8)
+        n = pk.shape[0]
+        codes = np.empty(n, dtype=np.int64)
+        events, done = [], 0
+        while True:
+            n_ev, got = ctypes.c_int(), ctypes.c_int64()
+            _check(load().xcorr_tracker_feed(self.handle, pk[done:].ctypes.data if n else None,
+                                             pk.shape[1] if pk.ndim == 2 else 16, n - done,
+                                             codes[done:].ctypes.data if n else None,
+                                             self._events, self._max, ctypes.byref(n_ev),
+                                             ctypes.byref(got)))
+            events += self._ev_list(n_ev.value, done)
+            done += got.value
+            if done >= n and n_ev.value < self._max:
+                return codes, events
+
+    def finish(self) -> list[dict]:
+        events = []
+        while True:
+            n_ev = ctypes.c_int()
+            _check(load().xcorr_tracker_finish(self.handle, self._events, self._max,
+                                               ctypes.byref(n_ev)))
+            events += self._ev_list(n_ev.value)
+            if n_ev.value < self._max:
+                return events
+
+    def counters(self) -> dict:
+        c = xcorr_packet_counters()
+        _check(load().xcorr_tracker_counters(self.handle, ctypes.byref(c)))
+        return _counters_dict(c)
+
+    def close(self) -> None:
+        if self.handle:
+            load().xcorr_tracker_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Stream:
+    """A streaming X-stage over a 4-bit plan: push packets, read dumps."""
+
+    def __init__(self, plan: "Plan", cfg: xcorr_stream_config):
+        self.plan, self.cfg = plan, cfg
+        self.handle = ctypes.c_void_p()
+        _check(load().xcorr_stream_create(ctypes.byref(self.handle), plan.handle,
+                                          ctypes.byref(cfg)))
+        self.packet_bytes = packet_bytes(cfg)
+        self.out_shape = (plan.n_channels, plan.info["n_pairs"], 2)
+
+    def acquire(self) -> tuple[int, int]:
+        """(host address, capacity in packets) of the next landing chunk."""
+        ptr, cap = ctypes.c_void_p(), ctypes.c_int64()
+        _check(load().xcorr_stream_acquire(self.handle, ctypes.byref(ptr), ctypes.byref(cap)))
+        return ptr.value, cap.value
+
+    def commit(self, n_packets: int) -> None:
+        _check(load().xcorr_stream_commit(self.handle, n_packets))
+
+    def push(self, packets) -> None:
+        """Copy packets (uint8 [n][packet bytes], host) through the landing chunks."""
+        import numpy as np
+        pk = np.ascontiguousarray(packets, dtype=np.uint8)
+        done = 0
+        while done < pk.shape[0]:
+            ptr, cap = self.acquire()
+            n = min(cap, pk.shape[0] - done)
+            ctypes.memmove(ptr, pk[done:done + n].ctypes.data, n * self.packet_bytes)
+            self.commit(n)
+            done += n
+
+    def flush(self) -> None:
+        _check(load().xcorr_stream_flush(self.handle))
+
+    def counters(self) -> tuple[dict, int]:
+        c, n = xcorr_packet_counters(), ctypes.c_int64()
+        _check(load().xcorr_stream_counters(self.handle, ctypes.byref(c), ctypes.byref(n)))
+        return _counters_dict(c), n.value
+
+    def wait_dump(self, k: int, timeout_ms: int = 60000, copy: bool = True) -> dict:
+        """Dump k (0-based): its record, with ``data`` an int32 [C][P][2] numpy copy."""
+        import numpy as np
+        r = xcorr_dump_record()
+        _check(load().xcorr_stream_wait_dump(self.handle, k, timeout_ms, ctypes.byref(r)))
+        out = {"index": r.index, "n_samples": r.n_samples, "lost_packets": r.lost_packets,
+               "latency_ms": r.latency_ms, "data": None}
+        if r.data and copy:
+            n = int(np.prod(self.out_shape))
+            buf = (ctypes.c_int32 * n).from_address(r.data)
+            out["data"] = np.frombuffer(buf, dtype=np.int32).reshape(self.out_shape).copy()
+        return out
+
+    def close(self) -> None:
+        if self.handle:
+            _check(load().xcorr_stream_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Batch:

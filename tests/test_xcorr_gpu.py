@@ -324,8 +324,8 @@ def test_every_launch_shape_is_exact(torch, variant, groups, x_streams):
 @pytest.mark.parametrize("n_sta,n_chan,n_time", [(8, 1, 1), (8, 2, 65), (64, 3, 300), (72, 2, 257),
                                                  (200, 2, 385), (256, 3, 1000)])
 def test_fused_4bit_kernel_bit_exact(torch, variant, n_sta, n_chan, n_time):
-    # N_i a multiple of 16: the unpack runs inside the X kernel (raw TMA tiles
-    # decoded on chip); ragged input blocks and time tails
+    # N_i a multiple of 16: the unpack runs inside the X kernel (raw bytes
+    # decoded on chip to offset E4M3 codes); ragged input blocks and time tails
     x = synth.uniform_ci4(n_time, n_chan, n_sta, seed=variant * 1000 + n_sta + n_time, lo=-8, hi=7)
     got, _ = run(torch, x, "tensor", tuning=(variant, 0, 2, 0))
     assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
@@ -338,6 +338,30 @@ def test_fused_and_planes_paths_agree_over_several_executes(torch, unfused):
     got, n = run(torch, x, "tensor", chunks=chunks, tuning=(1, 0, 2, unfused))
     assert n == sum(chunks)
     assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+FUSED_BLOCK = 37248  # samples per exactly-summed block of the fused kernel
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("pattern", ["max", "extremes"])
+def test_fused_exact_across_blocks_at_the_bound(torch, variant, pattern):
+    # Two full blocks and a tail.  "max": every sample 7 + 7i, so each block's
+    # offset sums reach 450 T, the largest the FP32 accumulator holds exactly;
+    # "extremes": components drawn from {-8, 7}.
+    n_time, n_chan, n_sta = 2 * FUSED_BLOCK + 77, 2, 16
+    shape = (n_time, n_chan, n_sta, 2)
+    if pattern == "max":
+        x = synth.pack_ci4(np.full(shape, 7), np.full(shape, 7))
+    else:
+        rng = np.random.default_rng(variant + 5)
+        x = synth.pack_ci4(np.where(rng.random(shape) < 0.5, -8, 7), np.where(rng.random(shape) < 0.5, -8, 7))
+    got, n = run(torch, x, "tensor", tuning=(variant, 0, 2, 0))
+    assert n == n_time
+    want = oracle.correlate(oracle.FMT_CI4, x)
+    if pattern == "max":
+        assert (want[..., 0] == 98 * n_time).all() and (want[..., 1] == 0).all()
+    assert np.array_equal(got, want)
 
 
 def test_fused_falls_back_for_unaligned_input(torch):
