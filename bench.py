@@ -550,6 +550,25 @@ def our_arm(args) -> int:
     return 0
 
 
+def h2d_ceiling(torch, nbytes: int, reps: int = 6) -> dict:
+    """Pinned host -> device copy rate of chunk-sized copies, on one stream and
+    on two streams at once (the link ceiling for the stream's input)."""
+    hp = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    dps = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    out = {}
+    for n_str in (1, 2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in range(reps):
+            for q in range(n_str):
+                with torch.cuda.stream(streams[q]):
+                    dps[q].copy_(hp, non_blocking=True)
+        torch.cuda.synchronize()
+        out[f"{n_str}_stream" + ("s" if n_str > 1 else "")] = n_str * reps * nbytes / (time.perf_counter() - t0) / 1e9
+    return out
+
+
 def stream_arm(args) -> int:
     """The streaming server of the paper's Fig. 4 on one GPU: an F-engine
     emulator fills the stream's pinned landing chunks with packets, the stream
@@ -616,6 +635,7 @@ def stream_arm(args) -> int:
     counters, _ = stream.counters()
     stream.close()
     plan.close()
+    h2d = h2d_ceiling(torch, cfg.chunk_packets * pb)
     # a sampled channel of the last dump against the oracle: 4 identical blocks
     import oracle
     c = 5
@@ -644,6 +664,7 @@ def stream_arm(args) -> int:
         "dump_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                             "max": lat[-1]},
         "packets": counters,
+        "h2d_ceiling_gbs": h2d,
         "sampled_channel_exact": exact,
         "clocks": clocks.summary(),
     }

@@ -10,17 +10,17 @@
  *     V[c][i][j] = sum_t x[t][c][i] * conj(x[t][c][j]),   0 <= j <= i < N_i
  *
  * with N_i = 2 * n_stations inputs, input i = 2 * station + pol (the paper's
- * N_i is "twice the number of antennas", Sec. 2.2.3).  The integration is the
+ * N_i counts two inputs per antenna, Sec. 2.2.3).  The integration is the
  * exact SUM over the samples given since the last reset; the paper's GPU
- * "averages" (Sec. 2.4, Sec. 4), and the caller divides by the sample count
+ * averages (Sec. 2.4, Sec. 4), and the caller divides by the sample count
  * returned with each dump.
  *
  * Input layout (Sec. 2.3 and Fig. 3: per time sample, every channel of every
  * input), sample order [time][channel][station][pol], one element per
  * complex sample:
  *   XCORR_IN_CI4   uint8: high nibble = real, low nibble = imaginary, each
- *                  4-bit two's complement in [-8, 7] (Sec. 2.3: "four bits
- *                  for each component"; the nibble order is this library's
+ *                  4-bit two's complement in [-8, 7] (Sec. 2.3: four bits
+ *                  per component; the nibble order is this library's
  *                  reading, the paper does not fix it).
  *   XCORR_IN_CI8   int8 pair (re, im), the unpacked 8-bit form of Sec. 2.4.
  *   XCORR_IN_CF32  float pair (re, im), spectra from a GPU F-stage (Sec. 1);
@@ -302,7 +302,7 @@ xcorr_status xcorr_batch_destroy(xcorr_batch batch);
  * placement is the corner turn the paper's capture and unpack threads do.
  * Packets may arrive in any order.  While the oldest block is incomplete,
  * packets of later blocks are held in their own ring blocks (the paper's
- * "stack"); when their number reaches stack_threshold, or a packet arrives for
+ * stack); when their number reaches stack_threshold, or a packet arrives for
  * a block past the ring, the oldest block is closed: its missing packets are
  * recorded lost and zero-filled, and it is correlated into the current dump.
  * A complete oldest block closes at once.  Every blocks_per_dump blocks (the
@@ -451,7 +451,7 @@ const char *xcorr_last_error(void);
 
 /*
  * Map a station pair and polarisation product to the packed triangle
- * (recovers the "baselines x four polarisation products" view of Eq. 4 from
+ * (recovers the view of Eq. 4, baselines times four polarisation products, from
  * the input-pair triangle).  V(a, p; b, q) = x_{a,p} conj(x_{b,q}) for
  * stations a >= b, pols p, q in {0, 1}.  *idx receives p(i, j) of the stored
  * pair and *conj is 1 when the requested product is the conjugate of the

@@ -18,11 +18,11 @@
  * [time][channel][station][pol].  The output is the packed lower triangle,
  * pair index i (i + 1) / 2 + j, with (re, im) interleaved, [channel][pair][2].
  * Integer inputs accumulate in int64 and float inputs in double; the result is
- * the integrated SUM over the K samples (the paper's GPU "averages"; the sum
+ * the integrated SUM over the K samples (the paper's GPU averages; the sum
  * keeps the result exact and the caller divides by K).
  *
  * The steps follow the paper's order: the corner turn and the widening of
- * 4-bit samples (Sec. 2.4, "unpacking"), then the cross multiplication.  Both
+ * 4-bit samples (Sec. 2.4, the unpacking step), then the cross multiplication.  Both
  * are written as plain loops; channels are independent (Sec. 2.1: the X-stage
  * is parallel in frequency) and are spread over POSIX threads.
  */

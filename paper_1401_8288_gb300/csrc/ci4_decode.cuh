@@ -2,7 +2,7 @@
 //
 // A CI4 byte holds a 4-bit two's-complement real part in its high nibble and
 // the imaginary part in its low nibble (the library's reading of the paper's
-// "4 bits real and 4 bits imaginary", Sec. 2.3).  Every value in [-8, 7] is an
+// four bits for each of the real and imaginary parts, Sec. 2.3).  Every value in [-8, 7] is an
 // exact E4M3 number, so these codes feed kind::f8f6f4 MMAs with the true
 // integers.  The lookups are byte permutes over two 8-entry tables.
 #pragma once

@@ -4,9 +4,10 @@
 // unpack-and-reorder and GPU threads over ring buffers of four sub-blocks.
 // Here the host only tracks headers (PacketTracker); the bytes go straight
 // to the GPU, where a scatter kernel does the placement and corner turn into a
-// device ring of blocks in the [t][c][i] order the X kernels read.  Three CUDA
+// device ring of blocks in the [t][c][i] order the X kernels read.  CUDA
 // streams overlap the stages the way the paper's threads do:
-//   copy    -- H2D of landing chunks, scatter, zero-fill of lost packets
+//   h2d x2  -- copies of landing chunks, alternating (two copy engines)
+//   copy    -- scatter of each landed chunk, zero-fill of lost packets
 //   compute -- the X-stage of each closed block, into a device dump buffer
 //   d2h     -- the copy of each finished dump to pinned host memory
 // Events order them: a block's X waits for its last scatter and zero-fill, a
@@ -142,7 +143,8 @@ struct xcorr_stream_s {
   int64_t* h_codes = nullptr;
   std::vector<void*> h_out;
   cudaStream_t s_copy = nullptr, s_comp = nullptr, s_d2h = nullptr;
-  std::vector<cudaEvent_t> chunk_done, slot_free, block_ready;
+  cudaStream_t s_h2d[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> chunk_done, chunk_landed, slot_free, block_ready;
   cudaEvent_t comp_done[2] = {nullptr, nullptr}, out_free[2] = {nullptr, nullptr};
   std::vector<xcorr_block_event> events;
   int64_t next_chunk = 0;
@@ -271,7 +273,9 @@ void free_stream(xcorr_stream s) {
   if (s->s_copy) cudaStreamSynchronize(s->s_copy);
   if (s->s_comp) cudaStreamSynchronize(s->s_comp);
   if (s->s_d2h) cudaStreamSynchronize(s->s_d2h);
-  for (auto* v : {&s->chunk_done, &s->slot_free, &s->block_ready})
+  for (cudaStream_t st : s->s_h2d)
+    if (st) cudaStreamSynchronize(st);
+  for (auto* v : {&s->chunk_done, &s->chunk_landed, &s->slot_free, &s->block_ready})
     for (auto ev : *v)
       if (ev) cudaEventDestroy(ev);
   for (int j = 0; j < 2; ++j) {
@@ -279,7 +283,7 @@ void free_stream(xcorr_stream s) {
     if (s->out_free[j]) cudaEventDestroy(s->out_free[j]);
     if (s->d_out[j]) cudaFree(s->d_out[j]);
   }
-  for (cudaStream_t st : {s->s_copy, s->s_comp, s->s_d2h})
+  for (cudaStream_t st : {s->s_copy, s->s_comp, s->s_d2h, s->s_h2d[0], s->s_h2d[1]})
     if (st) cudaStreamDestroy(st);
   if (s->ring) cudaFree(s->ring);
   if (s->bits) cudaFree(s->bits);
@@ -353,7 +357,9 @@ xcorr_status xcorr_stream_create(xcorr_stream* out, xcorr_plan plan, const xcorr
   if ((e = cudaMemset(s->bits, 0, bits_bytes)) != cudaSuccess) return fail_cuda("bitmap reset");
   if ((e = cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = cudaStreamCreateWithFlags(&s->s_d2h, cudaStreamNonBlocking)) != cudaSuccess)
+      (e = cudaStreamCreateWithFlags(&s->s_d2h, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&s->s_h2d[0], cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&s->s_h2d[1], cudaStreamNonBlocking)) != cudaSuccess)
     return fail_cuda("stream create");
   auto make_events = [&](std::vector<cudaEvent_t>& v, int n) {
     v.assign(n, nullptr);
@@ -361,7 +367,8 @@ xcorr_status xcorr_stream_create(xcorr_stream* out, xcorr_plan plan, const xcorr
       if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return false;
     return true;
   };
-  if (!make_events(s->chunk_done, cfg->n_chunks) || !make_events(s->slot_free, g.n_blocks) ||
+  if (!make_events(s->chunk_done, cfg->n_chunks) || !make_events(s->chunk_landed, cfg->n_chunks) ||
+      !make_events(s->slot_free, g.n_blocks) ||
       !make_events(s->block_ready, g.n_blocks))
     return fail_cuda("event create");
   for (int j = 0; j < 2; ++j)
@@ -401,9 +408,13 @@ xcorr_status xcorr_stream_commit(xcorr_stream s, int64_t n_packets) {
   int64_t* hc = s->h_codes + static_cast<int64_t>(k) * s->cfg.chunk_packets;
   int64_t* dc = s->d_codes + static_cast<int64_t>(k) * s->cfg.chunk_packets;
   cudaError_t e;
+  // the payload copy runs on one of two copy streams; the scatters wait for it
+  cudaStream_t h2d = s->s_h2d[(s->next_chunk - 1) & 1];
   if (n_packets > 0 &&
-      (e = cudaMemcpyAsync(s->d_landing + k * s->chunk_bytes, hp, n_packets * pb, cudaMemcpyHostToDevice,
-                           s->s_copy)) != cudaSuccess)
+      ((e = cudaMemcpyAsync(s->d_landing + k * s->chunk_bytes, hp, n_packets * pb, cudaMemcpyHostToDevice, h2d)) !=
+           cudaSuccess ||
+       (e = cudaEventRecord(s->chunk_landed[k], h2d)) != cudaSuccess ||
+       (e = cudaStreamWaitEvent(s->s_copy, s->chunk_landed[k], 0)) != cudaSuccess))
     return cuda_err(s, e, "chunk copy");
   int64_t done = 0;
   for (int guard = 0; done < n_packets || guard == 0; ++guard) {

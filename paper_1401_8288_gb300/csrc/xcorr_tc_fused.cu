@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       dec_bar_sync();
       const int buf = g & 1;
       const uint32_t use = static_cast<uint32_t>(g >> 1);
-      if (ok) ok = mbar_wait(&tempty[buf], (use & 1u) ^ 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_EMPTY);
+      if (ok) ok = mbar_wait_warp(&tempty[buf], (use & 1u) ^ 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_EMPTY);
       if (ok && (!diag || tid < 128)) {
         const int slot = diag ? 0 : tid >> 7, e = tid & 127;
         const int w0 = diag ? 0 : slot * 4, nw = diag ? 8 : 4;
@@ -503,7 +503,8 @@ cudaError_t launch_fused(const CUtensorMap& raw_map, const FParams& p, int grid,
 
 }  // namespace
 
-// Stage heights of the fused variants: 128 samples (2 raw + 2 decoded stages), 96 (2 + 3), 64 (4 + 4).
+// Stage heights of the fused variants: 128 samples (2 raw + 2 decoded stages), 96 (4 + 2), 64 (6 + 3):
+// deeper raw rings hide more TMA latency, deeper decoded rings more decoder jitter.
 int fused_stage_samples(int variant) { return variant == 0 ? 128 : variant == 1 ? 96 : 64; }
 
 int fused_launches(int n_time) { return n_time <= 0 ? 0 : (n_time + kFusedWindowCI4 - 1) / kFusedWindowCI4; }
@@ -538,8 +539,8 @@ cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int variant, int n_time
     cudaError_t e;
     switch (variant) {
       case 0: e = launch_fused<128, 2, 2>(raw_map, p, grid, stream); break;
-      case 1: e = launch_fused<96, 2, 3>(raw_map, p, grid, stream); break;
-      default: e = launch_fused<64, 4, 4>(raw_map, p, grid, stream); break;
+      case 1: e = launch_fused<96, 4, 2>(raw_map, p, grid, stream); break;
+      default: e = launch_fused<64, 6, 3>(raw_map, p, grid, stream); break;
     }
     if (e != cudaSuccess) return e;
   }
