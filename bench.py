@@ -431,8 +431,9 @@ def our_arm(args) -> int:
     host_out = torch.empty((n_chan, n_pairs, 2), dtype=out_dtype).pin_memory()
 
     def e2e_step():
-        xd.copy_(x_pin, non_blocking=True)
-        plan.execute_dump(xd, host_out, reset=True)
+        # xcorr_execute_dump_host: channel groups copied up, correlated and copied
+        # down in a pipeline (one piece for paths the fused kernel does not take)
+        plan.execute_dump_host(x_pin, host_out)
 
     for _ in range(max(args.warmup, 3)):
         e2e_step()
@@ -608,16 +609,29 @@ def stream_arm(args) -> int:
 
     stream = xcorr.Stream(plan, cfg)
     views = {}
+    host_s = {"acquire": 0.0, "emulator": 0.0, "commit": 0.0}
 
     def push_block(b):
+        # chunk buffer k always carries the k-th eighth of a block: written whole
+        # once, then only moved one block ahead in time per reuse
         for k in range(chunks_per_block):
+            t0 = time.perf_counter()
             ptr, cap = stream.acquire()
-            if ptr not in views:  # first use of this chunk: write whole packets
-                views[ptr] = np.ctypeslib.as_array((ctypes.c_uint8 * (cap * pb)).from_address(ptr)).reshape(cap, pb)
-                views[ptr][:] = packets[k * cap:(k + 1) * cap]
-            hdr = views[ptr][:, :8].view(np.uint64)
-            hdr[:, 0] = packets[k * cap:(k + 1) * cap, :8].view(np.uint64)[:, 0] + np.uint64(b * seq_per_block)
+            t1 = time.perf_counter()
+            if ptr not in views:
+                views[ptr] = b
+                dst = np.ctypeslib.as_array((ctypes.c_uint8 * (cap * pb)).from_address(ptr)).reshape(cap, pb)
+                dst[:] = packets[k * cap:(k + 1) * cap]
+                xcorr.xcorr_packets_advance(ptr, pb, cap, b * seq_per_block)
+            else:
+                xcorr.xcorr_packets_advance(ptr, pb, cap, (b - views[ptr]) * seq_per_block)
+                views[ptr] = b
+            t2 = time.perf_counter()
             stream.commit(cap)
+            t3 = time.perf_counter()
+            host_s["acquire"] += t1 - t0
+            host_s["emulator"] += t2 - t1
+            host_s["commit"] += t3 - t2
 
     warm_dumps = max(1, args.warmup // 4)
     n_dumps = max(2, args.steps)
@@ -625,6 +639,8 @@ def stream_arm(args) -> int:
         push_block(b)
     stream.wait_dump(warm_dumps - 1, timeout_ms=120000, copy=False)
     torch.cuda.synchronize()
+    for key in host_s:
+        host_s[key] = 0.0
     with ClockSampler(info.local_rank) as clocks:
         t0 = time.perf_counter()
         for b in range(warm_dumps * bpd, (warm_dumps + n_dumps) * bpd):
@@ -665,6 +681,7 @@ def stream_arm(args) -> int:
                             "max": lat[-1]},
         "packets": counters,
         "h2d_ceiling_gbs": h2d,
+        "host_ms_per_dump": {k: 1e3 * v / n_dumps for k, v in host_s.items()},
         "sampled_channel_exact": exact,
         "clocks": clocks.summary(),
     }

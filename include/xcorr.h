@@ -90,12 +90,14 @@ typedef struct xcorr_plan_s *xcorr_plan;
 
 /* Launch shape of the tensor-core path (xcorr_plan_set_tuning, xcorr_autotune). */
 typedef struct {
-    int stage_variant;  /* shared-memory ring: 0 = 3 x 64 KB, 1 = 4 x 48 KB, 2 = 6 x 32 KB stages */
+    int stage_variant;  /* shared-memory ring, 0 .. 3: planes path 0 = 3 x 64 KB, 1 (and 3) =
+                           4 x 48 KB, 2 = 6 x 32 KB stages; fused path see `unfused`           */
     int groups;         /* channel groups whose unpack overlaps the X kernel; 0 = automatic (<= 8) */
     int x_streams;      /* 1 or 2 streams the groups' X launches alternate over                 */
     int unfused;        /* 4-bit input: 0 = unpack on chip inside the X kernel where possible
-                           (N_i % 16 == 0, 16-byte aligned input, n_time <= 130,944;
-                           stage_variant then picks 128, 96 or 64-sample stages),
+                           (N_i % 16 == 0, 16-byte aligned input); stage_variant then picks
+                           raw / decoded rings of 128 x (2 + 2), 96 x (4 + 2), 64 x (6 + 3)
+                           samples with 8 decoder warps, or 96 x (4 + 2) with 12;
                            1 = always through E4M3 planes in HBM                            */
 } xcorr_tuning;
 
@@ -171,12 +173,34 @@ xcorr_status xcorr_execute_dump(xcorr_plan plan, const void *d_in, int n_time, v
                                 int out_on_device, unsigned flags, void *stream,
                                 int64_t *n_samples);
 
+/*
+ * One whole integration from host memory to host memory, with the copies
+ * overlapped with the X-stage: the channels are cut into n_groups groups (0 =
+ * the library's choice: at most 8, each copy row at least 64 KB, since copy
+ * engines move narrower 2-D rows at half rate); each group's input columns go up (a 2-D
+ * copy of its channels of every sample), are correlated, and its triangle
+ * comes back while later groups are still being copied or correlated.  The
+ * result equals copying the input to the device, xcorr_execute_dump with
+ * XCORR_DUMP_RESET, and copying the output back.  h_in: n_time samples in the
+ * input layout; h_out: [C][P][2] as xcorr_dump writes it.  Both should be
+ * pinned (cudaHostAlloc / cudaHostRegister), or the copies do not overlap.  The
+ * plan must hold no integration (nothing executed since the last reset) and
+ * still holds none afterwards.  Input that the fused 4-bit kernel cannot take
+ * (other formats, the CUDA-core engine, unaligned sizes) runs as one piece:
+ * the copy up, the X-stage and the copy down, in order.  The first call
+ * allocates a device copy of one input (max_time_per_exec samples), kept
+ * until xcorr_destroy.  Stream-ordered on `stream`.
+ * Errors: INVALID_ARG, OVERFLOW, OOM, CUDA, DEVICE.
+ */
+xcorr_status xcorr_execute_dump_host(xcorr_plan plan, const void *h_in, int n_time, void *h_out, int n_groups,
+                                     void *stream);
+
 /* Wait for the stream and report any kernel-side failure (DEVICE). */
 xcorr_status xcorr_sync(xcorr_plan plan, void *stream);
 
 /*
  * Fix the tensor path's launch shape (results do not depend on it).
- * Errors: INVALID_ARG (stage_variant not in [0, 2], groups not in [0, 8],
+ * Errors: INVALID_ARG (stage_variant not in [0, 3], groups not in [0, 8],
  * x_streams not 1 or 2), DEVICE.
  */
 xcorr_status xcorr_plan_set_tuning(xcorr_plan plan, const xcorr_tuning *tuning);
@@ -396,6 +420,14 @@ xcorr_status xcorr_packetize(const void *samples, int n_time, int n_channels, in
                              const xcorr_stream_config *cfg, int64_t first_time_block,
                              void *packets, int64_t capacity_packets, int64_t *n_packets);
 
+/*
+ * Add seq_delta to the sequence number of n packets (packet k's header at
+ * packets + k * stride, host memory): replays the same payloads as later time
+ * blocks, the way an F-engine emulator keeps a link busy without rewriting
+ * payloads.  Errors: INVALID_ARG.
+ */
+xcorr_status xcorr_packets_advance(void *packets, int64_t stride, int64_t n, int64_t seq_delta);
+
 typedef struct xcorr_stream_s *xcorr_stream;
 
 typedef struct {
@@ -442,6 +474,45 @@ xcorr_status xcorr_stream_wait_dump(xcorr_stream s, int64_t k, int timeout_ms, x
 
 /* Synchronise the stream's work and free it (not the plan).  NULL is a no-op. */
 xcorr_status xcorr_stream_destroy(xcorr_stream s);
+
+/*
+ * Baseline-dependent integration (Sec. 6: short baselines rotate their fringes
+ * slowly and can be integrated longer without decorrelation; per-baseline
+ * integration lengths lower the output data rate).  The triangle of input
+ * pairs is cut into 128 x 128 tile pairs: input blocks I >= J of 128 inputs,
+ * tile pair t = I (I + 1) / 2 + J, nb = ceil(N_i / 128) blocks, nb (nb + 1) / 2
+ * tile pairs.  Tile pair t integrates over cadence[t] >= 1 base integrations.
+ *
+ * A base integration is whatever was executed on the plan since its last
+ * reset.  xcorr_bdi_step then, in one pass over the triangle on the stream:
+ *  - adds the plan's integration into the running sums of every tile pair;
+ *  - resets the plan;
+ *  - emits the tile pairs due at this step, those with
+ *    (step + 1) % cadence[t] == 0, where steps count from 0.
+ *
+ * Output layout: out receives the due tile pairs as dense blocks, int32
+ * [n_due][C][128][128][2]. Row r, column q of block k is the pair
+ * (128 I_k + r, 128 J_k + q). It is zero where that pair is not stored: past
+ * N_i, or above the diagonal. The due tile pairs' running sums restart from
+ * zero.
+ *
+ * Host-side outputs: due[] (capacity nb (nb + 1) / 2) receives the emitted
+ * tile-pair indices in increasing order, samples[] their integration lengths,
+ * and *n_due their count. out may be device memory (out_on_device = 1) or host
+ * memory.
+ *
+ * Integer (CI4, CI8) plans only.  The running sums live in a device buffer of
+ * the plan's output size.
+ * Errors: INVALID_ARG, UNSUPPORTED (float input), OVERFLOW (a tile pair would
+ * integrate past the plan's exact bound; nothing changes), OOM, CUDA, DEVICE.
+ */
+typedef struct xcorr_bdi_s *xcorr_bdi;
+
+xcorr_status xcorr_bdi_create(xcorr_bdi *out, xcorr_plan plan, const int *cadence, int n_tile_pairs);
+xcorr_status xcorr_bdi_step(xcorr_bdi bdi, void *out, int out_on_device, void *stream, int *n_due, int *due,
+                            int64_t *samples);
+/* Synchronise the device and free the running sums.  NULL is a no-op. */
+xcorr_status xcorr_bdi_destroy(xcorr_bdi bdi);
 
 /* Synchronise the device, free the plan's memory and the plan.  NULL is a no-op. */
 xcorr_status xcorr_destroy(xcorr_plan plan);

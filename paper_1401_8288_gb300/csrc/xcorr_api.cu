@@ -60,6 +60,15 @@ void release(xcorr_plan plan) {
     if (ev) cudaEventDestroy(ev);
   plan->s_unpack = nullptr;
   plan->s_x[0] = plan->s_x[1] = nullptr;
+  if (plan->s_down) cudaStreamDestroy(plan->s_down);
+  plan->s_down = nullptr;
+  for (auto* evs : {plan->ev_up, plan->ev_group_done})
+    for (int g = 0; g < xc::kMaxGroups; ++g)
+      if (evs[g]) cudaEventDestroy(evs[g]);
+  if (plan->ev_down) cudaEventDestroy(plan->ev_down);
+  plan->ev_down = nullptr;
+  if (plan->host_stage) cudaFree(plan->host_stage);
+  plan->host_stage = nullptr;
   if (plan->acc) cudaFree(plan->acc);
   if (plan->planes) cudaFree(plan->planes);
   if (plan->exps) cudaFree(plan->exps);
@@ -140,13 +149,13 @@ xcorr_status run_execute(xcorr_plan plan, const void* d_in, int n_time, void* ta
     // 4-bit input with the unpack on chip: one launch per exact block, on the caller's stream
     if (ev && ((e = cudaEventRecord(ev[1], s)) != cudaSuccess || (e = cudaEventRecord(ev[2], s)) != cudaSuccess))
       return cuda_fail(e, "profile event");
-    e = xc::launch_xcorr_tc_fused_ci4(static_cast<const uint8_t*>(d_in), plan->tune_variant, n_time, C, N,
+    e = xc::launch_xcorr_tc_fused_ci4(static_cast<const uint8_t*>(d_in), C, plan->tune_variant, n_time, C, N,
                                       static_cast<int2*>(target), !target_fresh, plan->status, plan->num_sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "fused X kernel launch");
     if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return cuda_fail(e, "profile event");
     if (ev) plan->prof_ngroups[plan->prof_count % plan->prof_cap] = 1;
   } else if (plan->engine == XCORR_ENGINE_TENSOR) {
-    const int variant = plan->tune_variant;
+    const int variant = xc::planes_variant(plan->tune_variant);
     if (plan->tmap_ntime != n_time || plan->tmap_variant != variant) {
       std::string err;
       if (!xc::encode_plane_tmap(&plan->tmap, plan->planes, plan->elem_bytes, N, plan->ni_pad, n_time,
@@ -438,6 +447,91 @@ xcorr_status xcorr_execute_dump(xcorr_plan plan, const void* d_in, int n_time, v
   return XCORR_OK;
 }
 
+xcorr_status xcorr_execute_dump_host(xcorr_plan plan, const void* h_in, int n_time, void* h_out, int n_groups,
+                                     void* stream) {
+  xcorr_status st = check_execute(plan, h_in, n_time);
+  if (st != XCORR_OK) return st;
+  if (!h_out) return fail(XCORR_ERR_INVALID_ARG, "h_out is NULL");
+  if (!plan->fresh || plan->samples != 0)
+    return fail(XCORR_ERR_INVALID_ARG, "the plan holds an integration: dump it with XCORR_DUMP_RESET first");
+  if (n_groups < 0) return fail(XCORR_ERR_INVALID_ARG, "n_groups must be >= 0");
+  const int C = plan->cfg.n_channels, N = plan->n_inputs;
+  const size_t in_elem = plan->cfg.fmt == XCORR_IN_CI4 ? 1 : plan->cfg.fmt == XCORR_IN_CI8 ? 2 : 8;
+  const size_t chan_bytes = in_elem * N;  // one channel of one sample
+  const size_t row_bytes = chan_bytes * C;
+  const size_t stage_bytes = row_bytes * plan->cfg.max_time_per_exec;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (!plan->host_stage) {
+    if ((e = cudaMalloc(&plan->host_stage, stage_bytes)) != cudaSuccess) {
+      plan->host_stage = nullptr;
+      cudaGetLastError();
+      return fail(XCORR_ERR_OOM, "host-execute staging buffer: " + std::string(cudaGetErrorString(e)));
+    }
+    plan->host_stage_bytes = stage_bytes;
+    plan->device_bytes += stage_bytes;
+    if ((e = cudaStreamCreateWithFlags(&plan->s_down, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "stream create");
+    for (int g = 0; g < xc::kMaxGroups; ++g)
+      if ((e = cudaEventCreateWithFlags(&plan->ev_up[g], cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&plan->ev_group_done[g], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "event create");
+    if ((e = cudaEventCreateWithFlags(&plan->ev_down, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "event create");
+  }
+  uint8_t* stage = static_cast<uint8_t*>(plan->host_stage);
+  const size_t out_chan_bytes = static_cast<size_t>(plan->n_pairs) * 8;
+  if (!(plan->engine == XCORR_ENGINE_TENSOR && fused_applies(plan, stage))) {
+    // one piece: up, X-stage, down, in order on the caller's stream
+    if ((e = cudaMemcpyAsync(stage, h_in, row_bytes * n_time, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "input copy");
+    if ((st = run_execute(plan, stage, n_time, plan->acc, true, s)) != XCORR_OK) return st;
+    if ((e = cudaMemcpyAsync(h_out, plan->acc, out_chan_bytes * C, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return cuda_fail(e, "output copy");
+  } else {
+    // channel groups: group g goes up on s_unpack, is correlated on s_x[g % 2] (a
+    // launch can start on the SMs the previous one's tail leaves idle) and comes
+    // down on s_down while later groups are still moving
+    // by default as many groups as keep each 2-D copy row >= 64 KB: narrower rows
+    // halve the copy engines' rate (measured: 210 GB/s at 64 KB, 104 GB/s at 32 KB)
+    const size_t min_width = size_t(64) << 10;
+    int G = n_groups > 0 ? n_groups : static_cast<int>(row_bytes / min_width < 1 ? 1 : row_bytes / min_width);
+    G = G > xc::kMaxGroups ? xc::kMaxGroups : G;
+    G = G > C ? C : G;
+    if ((e = cudaEventRecord(plan->ev_fork, s)) != cudaSuccess) return cuda_fail(e, "fork event");
+    for (cudaStream_t t : {plan->s_unpack, plan->s_x[0], plan->s_x[1], plan->s_down})
+      if ((e = cudaStreamWaitEvent(t, plan->ev_fork, 0)) != cudaSuccess) return cuda_fail(e, "fork wait");
+    for (int g = 0; g < G; ++g) {
+      const int c0 = static_cast<int>(static_cast<int64_t>(C) * g / G);
+      const int c1 = static_cast<int>(static_cast<int64_t>(C) * (g + 1) / G);
+      if (c1 <= c0) continue;
+      const size_t off = chan_bytes * c0, width = chan_bytes * (c1 - c0);
+      cudaStream_t sx = plan->s_x[g & 1];
+      int2* out_g = static_cast<int2*>(plan->acc) + static_cast<int64_t>(c0) * plan->n_pairs;
+      if ((e = cudaMemcpy2DAsync(stage + off, row_bytes, static_cast<const uint8_t*>(h_in) + off, row_bytes, width,
+                                 n_time, cudaMemcpyHostToDevice, plan->s_unpack)) != cudaSuccess ||
+          (e = cudaEventRecord(plan->ev_up[g], plan->s_unpack)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(sx, plan->ev_up[g], 0)) != cudaSuccess)
+        return cuda_fail(e, "group input copy");
+      if ((e = xc::launch_xcorr_tc_fused_ci4(stage + off, C, plan->tune_variant, n_time, c1 - c0, N, out_g, false,
+                                             plan->status, plan->num_sms, sx)) != cudaSuccess)
+        return cuda_fail(e, "fused X kernel launch");
+      if ((e = cudaEventRecord(plan->ev_group_done[g], sx)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(plan->s_down, plan->ev_group_done[g], 0)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(static_cast<uint8_t*>(h_out) + out_chan_bytes * c0, out_g, out_chan_bytes * (c1 - c0),
+                               cudaMemcpyDeviceToHost, plan->s_down)) != cudaSuccess)
+        return cuda_fail(e, "group output copy");
+    }
+    // join: every group's copy-out is on s_down, after its X launch and its input copy
+    if ((e = cudaEventRecord(plan->ev_down, plan->s_down)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, plan->ev_down, 0)) != cudaSuccess)
+      return cuda_fail(e, "join");
+  }
+  if ((e = cudaMemcpyAsync(plan->status_host, plan->status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "status copy");
+  return XCORR_OK;
+}
+
 xcorr_status xcorr_sync(xcorr_plan plan, void* stream) {
   xcorr_status st = plan_ok(plan);
   if (st != XCORR_OK) return st;
@@ -479,8 +573,8 @@ xcorr_status xcorr_plan_set_tuning(xcorr_plan plan, const xcorr_tuning* t) {
   xcorr_status st = plan_ok(plan);
   if (st != XCORR_OK) return st;
   if (!t) return fail(XCORR_ERR_INVALID_ARG, "tuning is NULL");
-  if (t->stage_variant < 0 || t->stage_variant >= xc::kTcVariants)
-    return fail(XCORR_ERR_INVALID_ARG, "stage_variant must be in [0, 2]");
+  if (t->stage_variant < 0 || t->stage_variant >= xc::kFusedVariants)
+    return fail(XCORR_ERR_INVALID_ARG, "stage_variant must be in [0, 3]");
   if (t->groups < 0 || t->groups > xc::kMaxGroups) return fail(XCORR_ERR_INVALID_ARG, "groups must be in [0, 8]");
   if (t->x_streams != 1 && t->x_streams != 2) return fail(XCORR_ERR_INVALID_ARG, "x_streams must be 1 or 2");
   if (t->unfused != 0 && t->unfused != 1) return fail(XCORR_ERR_INVALID_ARG, "unfused must be 0 or 1");
@@ -520,7 +614,7 @@ xcorr_status xcorr_autotune(xcorr_plan plan, const void* d_in, int n_time, void*
   plan->tune_unfused = 0;
   const bool fused_ok = fused_applies(plan, d_in);
   for (int uf = fused_ok ? 0 : 1; uf <= 1 && st == XCORR_OK; ++uf)
-  for (int v = 0; v < xc::kTcVariants && st == XCORR_OK; ++v) {
+  for (int v = 0; v < (uf == 0 ? xc::kFusedVariants : xc::kTcVariants) && st == XCORR_OK; ++v) {
     for (int gi = 0; gi < 4 && st == XCORR_OK; ++gi) {
       for (int xs = 1; xs <= 2 && st == XCORR_OK; ++xs) {
         if (group_choices[gi] == 1 && xs == 2) continue;  // one group has one X launch

@@ -30,7 +30,10 @@ constexpr int kTcWindowBF16 = 384;
 // Offset-binary 4-bit operands u = t + 8 in [0, 15]: |sum_t (u_re u_re' + u_im u_im')| <= 450 T
 // stays below 2^24 for T <= 37,282; rounded down to a multiple of 384 (every stage height).
 constexpr int kFusedWindowCI4 = 37248;
-constexpr int kTcVariants = 3;  // stage shapes: 64 KB x 3, 48 KB x 4, 32 KB x 6
+constexpr int kTcVariants = 3;     // planes-path stage shapes: 64 KB x 3, 48 KB x 4, 32 KB x 6
+constexpr int kFusedVariants = 4;  // fused 4-bit kernel shapes (the tuning's stage_variant range)
+// The planes path's shape for a tuning's stage_variant (3 exists only for the fused kernel).
+inline int planes_variant(int v) { return v >= kTcVariants ? 1 : v; }
 constexpr int64_t kMaxIntegrationCF32 = INT64_C(16777216);  // FP32 per dump, widen beyond
 
 enum ExecMode : int { MODE_STORE = 0, MODE_ADD = 1, MODE_ATOMIC = 2 };
@@ -69,7 +72,7 @@ struct xcorr_plan_s {
   size_t device_bytes = 0;
 
   // tuning of the tensor path (xcorr_plan_set_tuning / xcorr_autotune); 0 = automatic
-  int tune_variant = 0;        // stage shape, 0 .. kTcVariants - 1
+  int tune_variant = 0;        // stage shape, 0 .. kFusedVariants - 1 (see planes_variant)
   int tune_groups = 0;         // channel groups, 0 = heuristic
   int tune_x_streams = 2;      // X launches alternate over 1 or 2 streams
   int tune_unfused = 0;        // 4-bit input: 1 = always through planes, 0 = fuse the unpack when possible
@@ -85,6 +88,14 @@ struct xcorr_plan_s {
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_unpacked[xc::kMaxGroups] = {};
   cudaEvent_t ev_x_done[2] = {nullptr, nullptr};
+  // host-to-host executes: device copy of the input, the copy-out stream and
+  // per-group events (made on first use)
+  void* host_stage = nullptr;
+  size_t host_stage_bytes = 0;
+  cudaStream_t s_down = nullptr;
+  cudaEvent_t ev_up[xc::kMaxGroups] = {};
+  cudaEvent_t ev_group_done[xc::kMaxGroups] = {};
+  cudaEvent_t ev_down = nullptr;
 
   // timing (xcorr_profile_enable): kProfileEvents per timed execute -- start,
   // end of the last unpack, then (begin, end) of each X launch
@@ -165,17 +176,20 @@ bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inp
                        int n_time, int max_time, int n_planes_total, int box_t, std::string* err);
 
 
-// Tensor map over the caller's CI4 input [t][c][i] (n_inputs % 16 == 0, 16-byte
-// aligned pointer): boxes of 128 inputs x 1 channel x box_t samples, 128-byte
-// swizzle (the fused kernel's raw tiles, and its L2 prefetches).
-bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int n_time, int box_t,
-                         std::string* err);
+// Tensor map over n_chan channels of a CI4 input [t][c][i] whose time rows hold
+// row_chans channels (n_inputs % 16 == 0, 16-byte aligned pointer to the first
+// channel): boxes of 128 inputs x 1 channel x box_t samples, 128-byte swizzle
+// (the fused kernel's raw tiles, and its L2 prefetches).
+bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int row_chans, int n_time,
+                         int box_t, std::string* err);
 // The fused 4-bit X kernel (unpack on chip, offset-binary operands): one
 // launch per kFusedWindowCI4 samples; n_inputs % 16 == 0, `in` 16-byte aligned.
 int fused_stage_samples(int variant);
 int fused_launches(int n_time);
-cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int variant, int n_time, int n_chan, int n_inputs,
-                                      int2* out, bool accumulate, int* status, int num_sms, cudaStream_t stream);
+// `in` points at the first of n_chan channels; time rows hold row_chans channels.
+cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
+                                      int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
+                                      cudaStream_t stream);
 
 // int8 (re, im) samples -> two BF16 planes [c][2][t][ni_pad] (exact).
 cudaError_t launch_unpack_ci8_bf16(const int8_t* in, uint16_t* planes, int n_time, int n_chan, int c0,

@@ -146,7 +146,7 @@ struct xcorr_stream_s {
   cudaStream_t s_h2d[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> chunk_done, chunk_landed, slot_free, block_ready;
   cudaEvent_t comp_done[2] = {nullptr, nullptr}, out_free[2] = {nullptr, nullptr};
-  std::vector<xcorr_block_event> events;
+  std::vector<xcorr_block_event> events, chunk_events;
   int64_t next_chunk = 0;
   int acquired = -1;
   // the dump being integrated
@@ -408,33 +408,39 @@ xcorr_status xcorr_stream_commit(xcorr_stream s, int64_t n_packets) {
   int64_t* hc = s->h_codes + static_cast<int64_t>(k) * s->cfg.chunk_packets;
   int64_t* dc = s->d_codes + static_cast<int64_t>(k) * s->cfg.chunk_packets;
   cudaError_t e;
-  // the payload copy runs on one of two copy streams; the scatters wait for it
-  cudaStream_t h2d = s->s_h2d[(s->next_chunk - 1) & 1];
-  if (n_packets > 0 &&
-      ((e = cudaMemcpyAsync(s->d_landing + k * s->chunk_bytes, hp, n_packets * pb, cudaMemcpyHostToDevice, h2d)) !=
-           cudaSuccess ||
-       (e = cudaEventRecord(s->chunk_landed[k], h2d)) != cudaSuccess ||
-       (e = cudaStreamWaitEvent(s->s_copy, s->chunk_landed[k], 0)) != cudaSuccess))
-    return cuda_err(s, e, "chunk copy");
+  // 1. track every header on the host: placement codes and block events
+  std::vector<xcorr_block_event>& evs = s->chunk_events;
+  evs.clear();
   int64_t done = 0;
   for (int guard = 0; done < n_packets || guard == 0; ++guard) {
     int n_ev = 0;
     const int64_t got = s->tracker->feed(hp + done * pb, pb, n_packets - done, hc + done, s->events.data(),
                                          static_cast<int>(s->events.size()), &n_ev);
-    if (got > 0 && (e = cudaMemcpyAsync(dc + done, hc + done, got * 8, cudaMemcpyHostToDevice, s->s_copy)) !=
-                       cudaSuccess)
-      return cuda_err(s, e, "code copy");
-    int64_t cursor = done;
     for (int q = 0; q < n_ev; ++q) {
-      const int64_t pos = done + s->events[q].position;
-      if ((st = scatter(s, k, cursor, pos)) != XCORR_OK) return st;
-      cursor = pos;
-      if ((st = handle_event(s, s->events[q])) != XCORR_OK) return st;
+      evs.push_back(s->events[q]);
+      evs.back().position += done;
     }
-    if ((st = scatter(s, k, cursor, done + got)) != XCORR_OK) return st;
     if (got == 0 && n_ev == 0 && done < n_packets) return xc::set_error(XCORR_ERR_INVALID_ARG, "tracker stalled");
     done += got;
   }
+  // 2. codes and payloads go up together on one of two copy streams (a copy
+  //    queued behind the scatters would wait for later chunks' transfers)
+  cudaStream_t h2d = s->s_h2d[(s->next_chunk - 1) & 1];
+  if (n_packets > 0 &&
+      ((e = cudaMemcpyAsync(dc, hc, n_packets * 8, cudaMemcpyHostToDevice, h2d)) != cudaSuccess ||
+       (e = cudaMemcpyAsync(s->d_landing + k * s->chunk_bytes, hp, n_packets * pb, cudaMemcpyHostToDevice, h2d)) !=
+           cudaSuccess ||
+       (e = cudaEventRecord(s->chunk_landed[k], h2d)) != cudaSuccess ||
+       (e = cudaStreamWaitEvent(s->s_copy, s->chunk_landed[k], 0)) != cudaSuccess))
+    return cuda_err(s, e, "chunk copy");
+  // 3. scatter between the events, in packet order
+  int64_t cursor = 0;
+  for (const xcorr_block_event& ev : evs) {
+    if ((st = scatter(s, k, cursor, ev.position)) != XCORR_OK) return st;
+    cursor = ev.position;
+    if ((st = handle_event(s, ev)) != XCORR_OK) return st;
+  }
+  if ((st = scatter(s, k, cursor, n_packets)) != XCORR_OK) return st;
   if ((e = cudaEventRecord(s->chunk_done[k], s->s_copy)) != cudaSuccess) return cuda_err(s, e, "chunk event");
   return XCORR_OK;
 }

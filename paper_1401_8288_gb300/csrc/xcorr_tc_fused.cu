@@ -37,30 +37,43 @@ namespace {
 
 constexpr int kBlk = 128;
 constexpr int kEpiWarps = 4;
-constexpr int kDecWarps = 8;
 constexpr int kDecWarp0 = 4;
-constexpr int kProducerWarp = 12;
-constexpr int kMmaWarp = 13;
-constexpr int kThreads = 448;
 constexpr int kChunk = 16;
 constexpr int kPitch = kChunk + 1;
 constexpr int kAccCols = 256;  // [Re | -Im]
 constexpr uint32_t kTmemCols = 512;
 constexpr int kStagingBytes = kEpiWarps * 32 * kPitch * 8;
 constexpr int kSumsBytes = 2 * 2 * kBlk * 8;            // [TMEM buffer][I, J][input] (P, Q)
-constexpr int kScratchBytes = kDecWarps * 8 * 16 * 8;   // [decoder warp][chunk][input] (P, Q)
 constexpr int kBarrierBytes = 256;
 constexpr uint32_t kNibbleTop = 0x88888888u;            // t -> t + 8 on every nibble
 constexpr uint32_t kLowNibbles = 0x0F0F0F0Fu;
 constexpr int kPrefetchSamples = 512;                   // L2 prefetch distance along time
 
-template <int KT, int RAW, int DEC>
+// Warp roles for DW decoder warps: 0-3 epilogue, 4 .. 3 + DW decoders, then
+// the TMA producer and the MMA warp.
+template <int DW>
+struct Roles {
+  static constexpr int kDecWarps = DW;
+  static constexpr int kProducerWarp = kDecWarp0 + DW;
+  static constexpr int kMmaWarp = kDecWarp0 + DW + 1;
+  static constexpr int kThreads = (kDecWarp0 + DW + 2) * 32;
+  static constexpr int kDecThreads = DW * 32;
+  static constexpr int kTileThreads = DW * 16;                 // off the diagonal: one tile per half
+  static constexpr int kScratchBytes = DW * 8 * 16 * 8;        // [decoder warp][chunk][input] (P, Q)
+  static_assert(DW % 2 == 0, "two halves of decoder warps");
+};
+
+template <int KT, int RAW, int DEC, int DW>
 struct FGeom {
   static constexpr int kTile = KT * kBlk;        // one 128-input x KT-sample tile, raw or decoded
   static constexpr int kRawStage = 2 * kTile;    // raw I, raw J
   static constexpr int kDecStage = 4 * kTile;    // Xr_I, Xi_I, Xr_J, Xi_J
   static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kDecStage + kStagingBytes + kSumsBytes +
-                               kScratchBytes + kBarrierBytes;
+                               Roles<DW>::kScratchBytes + kBarrierBytes;
+  // rows per thread and stage off / on the diagonal (8 threads per 128-byte row)
+  static constexpr int kRowsOff = KT / (Roles<DW>::kTileThreads / 8);
+  static constexpr int kRowsDiag = KT / (Roles<DW>::kDecThreads / 8);
+  static_assert(KT % (Roles<DW>::kDecThreads / 8) == 0, "whole rows per decoder thread");
   static constexpr int kSteps = KT / 32;         // MMA steps (32 samples) per stage
   static_assert(KT % 32 == 0, "stage must hold whole MMA steps");
   static_assert(kSmem <= 232448, "shared memory budget");
@@ -76,6 +89,7 @@ struct FParams {
   int accumulate;      // add into out (else store)
   int2* out;
   int* status;
+  uint32_t one;        // 1: a multiplier the compiler cannot fold (see lane_add)
 };
 
 __device__ __forceinline__ void tile_pair(int p, int& I, int& J) {
@@ -122,15 +136,24 @@ __device__ __forceinline__ void prefetch_stage(const CUtensorMap* raw_map, const
 }
 
 // The decoder warps' own barrier (id 1), and its OR-reduction form.
-__device__ __forceinline__ void dec_bar_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-__device__ __forceinline__ bool dec_bar_or(bool v) {
+__device__ __forceinline__ void dec_bar_sync(uint32_t n_threads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(n_threads) : "memory");
+}
+__device__ __forceinline__ bool dec_bar_or(bool v, uint32_t n_threads) {
   uint32_t r;
   asm volatile(
-      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, 1, 256, q;\nselp.u32 %0, 1, 0, p;\n}"
+      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, 1, %2, q;\nselp.u32 %0, 1, 0, p;\n}"
       : "=r"(r)
-      : "r"(static_cast<uint32_t>(v))
+      : "r"(static_cast<uint32_t>(v)), "r"(n_threads)
       : "memory");
   return r != 0;
+}
+
+// a += b as an integer multiply-add by `one` (== 1 at run time).  The decoders'
+// byte-lane sums then issue on the FMA pipe instead of the ALU pipe, which the
+// decode itself keeps busy.
+__device__ __forceinline__ void lane_add(uint32_t& a, uint32_t b, uint32_t one) {
+  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(a) : "r"(b), "r"(one));
 }
 
 // Four CI4 bytes -> four offset E4M3 real codes and four imaginary codes.
@@ -146,13 +169,14 @@ __device__ __forceinline__ void offset_codes(uint32_t w, uint32_t& re, uint32_t&
 // same 128-byte swizzle), so the thread reads and writes offset `pos` of each
 // row.  Returns the chunk's per-input sums in 16-bit lanes (word e/2, half
 // e%2 holds input e); false if a wait gave up.
-template <int KT, int RAW, int DEC, int R>
+template <int KT, int RAW, int DEC, int DW, int R>
 __device__ __forceinline__ bool decode_item(const FParams& p, const uint8_t* raw, uint8_t* dec, uint64_t* raw_full,
                                             uint64_t* raw_empty, uint64_t* dec_full, uint64_t* dec_empty,
                                             volatile int* abort_flag, int& r, uint32_t& rph, int& d, uint32_t& dph,
                                             int slot, int tp, int lane, uint32_t (&s_re)[8], uint32_t (&s_im)[8]) {
-  using G = FGeom<KT, RAW, DEC>;
-  constexpr int kStep = KT / R;  // 16 or 32: a multiple of 8, so every row of the thread has the same swizzle
+  using G = FGeom<KT, RAW, DEC, DW>;
+  constexpr int kStep = KT / R;  // a multiple of 8, so every row of the thread has the same swizzle
+  static_assert(kStep % 8 == 0, "row step must keep the swizzle phase");
   const int L = tp & 7, phase = tp >> 3;
   const int pos = (L ^ (phase & 7)) << 4;  // 128-byte swizzle: chunk L of row r sits at chunk L ^ (r % 8)
 #pragma unroll
@@ -175,8 +199,10 @@ __device__ __forceinline__ bool decode_item(const FParams& p, const uint8_t* raw
       offset_codes(v[k].y, re.y, im.y);
       offset_codes(v[k].z, re.z, im.z);
       offset_codes(v[k].w, re.w, im.w);
-      a_re[0] += re.x, a_re[1] += re.y, a_re[2] += re.z, a_re[3] += re.w;
-      a_im[0] += im.x, a_im[1] += im.y, a_im[2] += im.z, a_im[3] += im.w;
+      lane_add(a_re[0], re.x, p.one), lane_add(a_re[1], re.y, p.one);
+      lane_add(a_re[2], re.z, p.one), lane_add(a_re[3], re.w, p.one);
+      lane_add(a_im[0], im.x, p.one), lane_add(a_im[1], im.y, p.one);
+      lane_add(a_im[2], im.z, p.one), lane_add(a_im[3], im.w, p.one);
       const int off = (phase + k * kStep) * 128;
       *reinterpret_cast<uint4*>(re_t + off) = re;
       *reinterpret_cast<uint4*>(im_t + off) = im;
@@ -184,10 +210,10 @@ __device__ __forceinline__ bool decode_item(const FParams& p, const uint8_t* raw
     // widen to 16-bit lanes: inputs (4q, 4q+1) -> word 2q, (4q+2, 4q+3) -> word 2q+1
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      s_re[2 * q] += __byte_perm(a_re[q], 0u, 0x4140);
-      s_re[2 * q + 1] += __byte_perm(a_re[q], 0u, 0x4342);
-      s_im[2 * q] += __byte_perm(a_im[q], 0u, 0x4140);
-      s_im[2 * q + 1] += __byte_perm(a_im[q], 0u, 0x4342);
+      lane_add(s_re[2 * q], __byte_perm(a_re[q], 0u, 0x4140), p.one);
+      lane_add(s_re[2 * q + 1], __byte_perm(a_re[q], 0u, 0x4342), p.one);
+      lane_add(s_im[2 * q], __byte_perm(a_im[q], 0u, 0x4140), p.one);
+      lane_add(s_im[2 * q + 1], __byte_perm(a_im[q], 0u, 0x4342), p.one);
     }
     // the MMA reads the tiles through the async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -208,10 +234,11 @@ __device__ __forceinline__ bool decode_item(const FParams& p, const uint8_t* raw
   return true;
 }
 
-template <int KT, int RAW, int DEC>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int KT, int RAW, int DEC, int DW>
+__global__ void __launch_bounds__(Roles<DW>::kThreads, 1)
     xcorr_tc_fused_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ FParams p) {
-  using G = FGeom<KT, RAW, DEC>;
+  using G = FGeom<KT, RAW, DEC, DW>;
+  using W = Roles<DW>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* raw = smem;
@@ -219,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int2* staging = reinterpret_cast<int2*>(dec + DEC * G::kDecStage);
   int2* sums = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(staging) + kStagingBytes);  // [2][2][128]
   int2* scratch = sums + 2 * 2 * kBlk;                                                           // [8][8][16]
-  uint64_t* raw_full = reinterpret_cast<uint64_t*>(scratch + kDecWarps * 8 * 16);
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(scratch + DW * 8 * 16);
   uint64_t* raw_empty = raw_full + RAW;
   uint64_t* dec_full = raw_empty + RAW;
   uint64_t* dec_empty = dec_full + DEC;
@@ -234,10 +261,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < RAW; ++s) {
       mbar_init(&raw_full[s], 1);
-      mbar_init(&raw_empty[s], kDecWarps);
+      mbar_init(&raw_empty[s], DW);
     }
     for (int s = 0; s < DEC; ++s) {
-      mbar_init(&dec_full[s], kDecWarps);
+      mbar_init(&dec_full[s], DW);
       mbar_init(&dec_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -249,14 +276,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == kMmaWarp) tmem_alloc(tslot, kTmemCols);
+  if (warp == W::kMmaWarp) tmem_alloc(tslot, kTmemCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const int n_items = p.n_chan * p.n_tile_pairs;
 
-  if (warp == kProducerWarp) {
+  if (warp == W::kProducerWarp) {
     if (lane == 0) {
       constexpr int kAhead = kPrefetchSamples / KT;  // L2 prefetch runs this many stages ahead of the loads
       prefetch_tmap(&raw_map);
@@ -296,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int q = 0; q < RAW; ++q)
         if (filled & (1u << q)) mbar_wait(&raw_full[q], fill_parity[q], &never, p.status, DEV_TIMEOUT_DRAIN);
     }
-  } else if (warp >= kDecWarp0 && warp < kDecWarp0 + kDecWarps) {
+  } else if (warp >= kDecWarp0 && warp < kDecWarp0 + DW) {
     const int tid = (warp - kDecWarp0) * 32 + lane;
     const int dw = warp - kDecWarp0;
     int r = 0, d = 0, g = 0;
@@ -305,12 +332,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       const Item cur = item_at(p, item, n_items);
       const bool diag = cur.diag;
       uint32_t s_re[8], s_im[8];
-      // off the diagonal, threads 0-127 take tile I and 128-255 tile J; on it, all take tile I
+      // off the diagonal the first half of the threads take tile I and the second half tile J;
+      // on it, all take tile I
       const bool ok_dec =
-          diag ? decode_item<KT, RAW, DEC, KT / 32>(p, raw, dec, raw_full, raw_empty, dec_full, dec_empty, abort_flag,
-                                                    r, rph, d, dph, 0, tid, lane, s_re, s_im)
-               : decode_item<KT, RAW, DEC, KT / 16>(p, raw, dec, raw_full, raw_empty, dec_full, dec_empty, abort_flag,
-                                                    r, rph, d, dph, tid >> 7, tid & 127, lane, s_re, s_im);
+          diag ? decode_item<KT, RAW, DEC, DW, G::kRowsDiag>(p, raw, dec, raw_full, raw_empty, dec_full, dec_empty,
+                                                             abort_flag, r, rph, d, dph, 0, tid, lane, s_re, s_im)
+               : decode_item<KT, RAW, DEC, DW, G::kRowsOff>(p, raw, dec, raw_full, raw_empty, dec_full, dec_empty,
+                                                            abort_flag, r, rph, d, dph, tid / W::kTileThreads,
+                                                            tid % W::kTileThreads, lane, s_re, s_im);
       bool ok = ok_dec;
       // per-input sums of this item: within the warp, lanes L, L+8, L+16, L+24 hold chunk L
       int2 pq[16];
@@ -331,13 +360,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int e = 0; e < 16; ++e) scratch[(dw * 8 + lane) * 16 + e] = pq[e];
       }
-      dec_bar_sync();
+      dec_bar_sync(W::kDecThreads);
       const int buf = g & 1;
       const uint32_t use = static_cast<uint32_t>(g >> 1);
       if (ok) ok = mbar_wait_warp(&tempty[buf], (use & 1u) ^ 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_EMPTY);
-      if (ok && (!diag || tid < 128)) {
+      // thread (slot, e) of the first 256 (128 on the diagonal) sums input e of
+      // its tile over the decoder warps that covered that tile
+      if (ok && tid < (diag ? 128 : 256)) {
         const int slot = diag ? 0 : tid >> 7, e = tid & 127;
-        const int w0 = diag ? 0 : slot * 4, nw = diag ? 8 : 4;
+        const int w0 = diag ? 0 : slot * (DW / 2), nw = diag ? DW : DW / 2;
         int2 s = make_int2(0, 0);
         for (int w = w0; w < w0 + nw; ++w) {
           const int2 x = scratch[(w * 8 + (e >> 4)) * 16 + (e & 15)];
@@ -346,10 +377,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         sums[(buf * 2 + slot) * kBlk + e] = s;
       }
-      if (dec_bar_or(!ok || *abort_flag)) break;
+      if (dec_bar_or(!ok || *abort_flag, W::kDecThreads)) break;
       if (tid == 0) mbar_arrive(&sfull[buf]);
     }
-  } else if (warp == kMmaWarp) {
+  } else if (warp == W::kMmaWarp) {
     if (lane == 0) {
       const uint32_t id256 = instr_desc(kTypeE4M3, true, 128, 256, false);
       const uint32_t id128 = instr_desc(kTypeE4M3, true, 128, 128, false);
@@ -478,16 +509,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc_fence_before();
   __syncthreads();
-  if (warp == kMmaWarp) {
+  if (warp == W::kMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);
   }
 }
 
-template <int KT, int RAW, int DEC>
+template <int KT, int RAW, int DEC, int DW>
 cudaError_t launch_fused(const CUtensorMap& raw_map, const FParams& p, int grid, cudaStream_t stream) {
-  using G = FGeom<KT, RAW, DEC>;
-  auto kern = xcorr_tc_fused_kernel<KT, RAW, DEC>;
+  using G = FGeom<KT, RAW, DEC, DW>;
+  auto kern = xcorr_tc_fused_kernel<KT, RAW, DEC, DW>;
   static int attr_device = -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -497,20 +528,22 @@ cudaError_t launch_fused(const CUtensorMap& raw_map, const FParams& p, int grid,
     if (e != cudaSuccess) return e;
     attr_device = dev;
   }
-  kern<<<grid, kThreads, G::kSmem, stream>>>(raw_map, p);
+  kern<<<grid, Roles<DW>::kThreads, G::kSmem, stream>>>(raw_map, p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// Stage heights of the fused variants: 128 samples (2 raw + 2 decoded stages), 96 (4 + 2), 64 (6 + 3):
-// deeper raw rings hide more TMA latency, deeper decoded rings more decoder jitter.
-int fused_stage_samples(int variant) { return variant == 0 ? 128 : variant == 1 ? 96 : 64; }
+// The fused variants: 128 samples (2 raw + 2 decoded stages), 96 (4 + 2), 64 (6 + 3), all with
+// 8 decoder warps, and 96 (4 + 2) with 12.  Deeper raw rings hide more TMA latency, deeper
+// decoded rings more decoder jitter, more decoder warps more of the decode's latency.
+int fused_stage_samples(int variant) { return variant == 0 ? 128 : variant == 2 ? 64 : 96; }
 
 int fused_launches(int n_time) { return n_time <= 0 ? 0 : (n_time + kFusedWindowCI4 - 1) / kFusedWindowCI4; }
 
-cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int variant, int n_time, int n_chan, int n_inputs,
-                                      int2* out, bool accumulate, int* status, int num_sms, cudaStream_t stream) {
+cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
+                                      int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
+                                      cudaStream_t stream) {
   const int nb = (n_inputs + kBlk - 1) / kBlk;
   const int kt = fused_stage_samples(variant);
   if (n_time <= 0 || n_inputs % 16 != 0 || reinterpret_cast<uintptr_t>(in) % 16 != 0 ||
@@ -518,17 +551,19 @@ cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int variant, int n_time
     return cudaErrorInvalidValue;
   FParams p{};
   p.in = in;
-  p.row_stride = (int64_t)n_chan * n_inputs;
+  p.row_stride = (int64_t)row_chans * n_inputs;
   p.n_chan = n_chan;
   p.n_inputs = n_inputs;
   p.n_tile_pairs = nb * (nb + 1) / 2;
   p.n_pairs = (int64_t)n_inputs * (n_inputs + 1) / 2;
   p.out = out;
   p.status = status;
+  p.one = 1u;
   const int64_t items = (int64_t)n_chan * p.n_tile_pairs;
   const int grid = static_cast<int>(items < num_sms ? items : num_sms);
   CUtensorMap raw_map;
-  if (!encode_raw_ci4_tmap(&raw_map, in, n_inputs, n_chan, n_time, kt, nullptr)) return cudaErrorInvalidValue;
+  if (row_chans < n_chan || !encode_raw_ci4_tmap(&raw_map, in, n_inputs, n_chan, row_chans, n_time, kt, nullptr))
+    return cudaErrorInvalidValue;
   // one exactly-summed block per launch; later blocks add into the first
   for (int t0 = 0; t0 < n_time; t0 += kFusedWindowCI4) {
     const int len = n_time - t0 < kFusedWindowCI4 ? n_time - t0 : kFusedWindowCI4;
@@ -538,9 +573,10 @@ cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int variant, int n_time
     p.accumulate = (accumulate || t0 > 0) ? 1 : 0;
     cudaError_t e;
     switch (variant) {
-      case 0: e = launch_fused<128, 2, 2>(raw_map, p, grid, stream); break;
-      case 1: e = launch_fused<96, 4, 2>(raw_map, p, grid, stream); break;
-      default: e = launch_fused<64, 6, 3>(raw_map, p, grid, stream); break;
+      case 0: e = launch_fused<128, 2, 2, 8>(raw_map, p, grid, stream); break;
+      case 1: e = launch_fused<96, 4, 2, 8>(raw_map, p, grid, stream); break;
+      case 2: e = launch_fused<64, 6, 3, 8>(raw_map, p, grid, stream); break;
+      default: e = launch_fused<96, 4, 2, 12>(raw_map, p, grid, stream); break;
     }
     if (e != cudaSuccess) return e;
   }

@@ -147,14 +147,15 @@ int64_t PacketTracker::feed(const uint8_t* packets, int64_t stride, int64_t n, i
       codes[k] = -1;
       continue;
     }
-    // events this packet needs: closes to make room in the ring, and an open
-    const int64_t first = oldest_ < 0 ? b : oldest_;
-    const int64_t n_close = b >= first + g_.n_blocks ? b - (first + g_.n_blocks) + 1 : 0;
-    const int s = static_cast<int>(b % g_.n_blocks);
-    const bool opens = n_close > 0 || slot_block_[s] != b;
-    if (*n_ev + n_close + (opens ? 1 : 0) > max_ev) return k;
+    // events this packet needs: closes to make room in the ring, then an open;
+    // when the event buffer fills first, the packet is retried by the next call
     if (oldest_ < 0) oldest_ = b;
-    for (int64_t q = 0; q < n_close; ++q) close_oldest(k, ev, n_ev);
+    while (b >= oldest_ + g_.n_blocks) {
+      if (*n_ev >= max_ev) return k;
+      close_oldest(k, ev, n_ev);
+    }
+    const int s = static_cast<int>(b % g_.n_blocks);
+    if (slot_block_[s] != b && *n_ev >= max_ev) return k;
     if (slot_block_[s] != b) {
       slot_block_[s] = b;
       slot_recv_[s] = 0;
@@ -285,6 +286,14 @@ xcorr_status xcorr_packetize(const void* samples, int n_time, int n_channels, in
         out += g.packet_bytes;
       }
   *n_packets = total;
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_packets_advance(void* packets, int64_t stride, int64_t n, int64_t seq_delta) {
+  if ((n > 0 && !packets) || n < 0 || stride < XCORR_PACKET_HEADER_BYTES)
+    return xc::set_error(XCORR_ERR_INVALID_ARG, "invalid packets_advance arguments");
+  uint8_t* p = static_cast<uint8_t*>(packets);
+  for (int64_t k = 0; k < n; ++k, p += stride) xc::store_le64(p, xc::load_le64(p) + static_cast<uint64_t>(seq_delta));
   return XCORR_OK;
 }
 

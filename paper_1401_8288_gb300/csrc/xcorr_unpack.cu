@@ -135,15 +135,15 @@ bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inp
   return true;
 }
 
-bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int n_time, int box_t,
-                         std::string* err) {
+bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int row_chans, int n_time,
+                         int box_t, std::string* err) {
   auto fn = encode_tiled_fn(err);
   if (!fn) return false;
   std::memset(map, 0, sizeof(*map));
   // the caller's [t][c][i] bytes: dim0 input, dim1 channel, dim2 time; a box is
   // 128 inputs x 1 channel x box_t samples = box_t rows of 128 bytes
   cuuint64_t dims[3] = {(cuuint64_t)n_inputs, (cuuint64_t)n_chan, (cuuint64_t)n_time};
-  cuuint64_t strides[2] = {(cuuint64_t)n_inputs, (cuuint64_t)n_inputs * (cuuint64_t)n_chan};
+  cuuint64_t strides[2] = {(cuuint64_t)n_inputs, (cuuint64_t)n_inputs * (cuuint64_t)row_chans};
   cuuint32_t box[3] = {128, 1, (cuuint32_t)box_t};
   cuuint32_t elem_strides[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(in), dims, strides, box, elem_strides,

@@ -36,7 +36,8 @@ EXPORTS = ("xcorr_plan_create", "xcorr_execute", "xcorr_dump", "xcorr_sync", "xc
            "xcorr_tracker_feed", "xcorr_tracker_finish", "xcorr_tracker_counters",
            "xcorr_tracker_destroy", "xcorr_packetize", "xcorr_stream_create", "xcorr_stream_acquire",
            "xcorr_stream_commit", "xcorr_stream_flush", "xcorr_stream_counters",
-           "xcorr_stream_wait_dump", "xcorr_stream_destroy")
+           "xcorr_stream_wait_dump", "xcorr_stream_destroy", "xcorr_packets_advance",
+           "xcorr_execute_dump_host", "xcorr_bdi_create", "xcorr_bdi_step", "xcorr_bdi_destroy")
 XCORR_PACKET_HEADER_BYTES = 16
 XCORR_EVENT_OPEN, XCORR_EVENT_CLOSE = 1, 2
 PEAK_KINDS = {"tc_e4m3": 0, "tc_bf16": 1, "mma_sync_s8": 2, "dp4a": 3}
@@ -152,6 +153,12 @@ def load():
                                           ctypes.POINTER(i64)],
                 "xcorr_stream_wait_dump": [vp, i64, i, ctypes.POINTER(xcorr_dump_record)],
                 "xcorr_stream_destroy": [vp],
+                "xcorr_packets_advance": [vp, i64, i64, i64],
+                "xcorr_execute_dump_host": [vp, vp, i, vp, i, vp],
+                "xcorr_bdi_create": [ctypes.POINTER(vp), vp, ctypes.POINTER(i), i],
+                "xcorr_bdi_step": [vp, vp, i, vp, ctypes.POINTER(i), ctypes.POINTER(i),
+                                   ctypes.POINTER(i64)],
+                "xcorr_bdi_destroy": [vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -198,6 +205,11 @@ def xcorr_execute_dump(plan, d_in: int, n_time: int, out: int, out_on_device: bo
     _check(load().xcorr_execute_dump(plan, d_in, n_time, out, int(out_on_device), flags, stream,
                                      ctypes.byref(n)))
     return n.value
+
+
+def xcorr_execute_dump_host(plan, h_in: int, n_time: int, h_out: int, n_groups: int = 0,
+                            stream: int = 0) -> None:
+    _check(load().xcorr_execute_dump_host(plan, h_in, n_time, h_out, n_groups, stream))
 
 
 def xcorr_sync(plan, stream: int = 0) -> None:
@@ -341,6 +353,11 @@ def xcorr_packetize(samples, cfg: xcorr_stream_config, first_time_block: int = 0
     return out[:n.value]
 
 
+def xcorr_packets_advance(address: int, stride: int, n: int, seq_delta: int) -> None:
+    """Add seq_delta to the sequence numbers of n packets at a host address."""
+    _check(load().xcorr_packets_advance(address, stride, n, seq_delta))
+
+
 class Tracker:
     """Host-side packet tracking (no GPU): placement codes and block events."""
 
@@ -468,6 +485,44 @@ class Stream:
         self.close()
 
 
+class BDI:
+    """Baseline-dependent integration over a plan: one cadence per 128 x 128
+    tile pair; ``step()`` after each base integration returns the due tile
+    pairs as dense int32 [n_due][C][128][128][2] blocks (on the device)."""
+
+    def __init__(self, plan: "Plan", cadence):
+        torch = plan._torch
+        self.plan, self._torch = plan, torch
+        cad = [int(c) for c in cadence]
+        self.n_tp = len(cad)
+        arr = (ctypes.c_int * self.n_tp)(*cad)
+        self.handle = ctypes.c_void_p()
+        _check(load().xcorr_bdi_create(ctypes.byref(self.handle), plan.handle, arr, self.n_tp))
+
+    def step(self, stream=None):
+        """(blocks tensor [n_due][C][128][128][2], due tile pairs, their sample counts)."""
+        torch = self._torch
+        n = ctypes.c_int()
+        due = (ctypes.c_int * self.n_tp)()
+        smp = (ctypes.c_int64 * self.n_tp)()
+        out = torch.empty((self.n_tp, self.plan.n_channels, 128, 128, 2), dtype=torch.int32, device="cuda")
+        _check(load().xcorr_bdi_step(self.handle, out.data_ptr(), 1, self.plan._stream(stream),
+                                     ctypes.byref(n), due, smp))
+        k = n.value
+        return out[:k], list(due[:k]), list(smp[:k])
+
+    def close(self) -> None:
+        if self.handle:
+            load().xcorr_bdi_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class Batch:
     """Several 4+4-bit correlations of uneven size in one tensor-core launch.
 
@@ -586,6 +641,21 @@ class Plan:
         flags = (XCORR_DUMP_RESET if reset else 0) | (XCORR_DUMP_ADD_WIDE if wide else 0)
         self.samples = xcorr_execute_dump(self.handle, x.data_ptr(), x.shape[0], out.data_ptr(),
                                           out.is_cuda, flags, self._stream(stream))
+        return out
+
+    def execute_dump_host(self, x, out=None, n_groups: int = 0, stream=None):
+        """One integration from host memory to host memory, copies overlapped with
+        the X-stage: x is a CPU tensor in the input layout (pin it for overlap);
+        returns (or fills) a CPU [C][P][2] tensor.  Complete after sync()."""
+        torch = self._torch
+        if x.is_cuda or not x.is_contiguous():
+            raise ValueError("input must be a contiguous host tensor")
+        if out is None:
+            out = torch.empty((self.n_channels, self.info["n_pairs"], 2), dtype=self._out_dtype(False),
+                              pin_memory=True)
+        xcorr_execute_dump_host(self.handle, x.data_ptr(), x.shape[0], out.data_ptr(), n_groups,
+                                self._stream(stream))
+        self.samples = x.shape[0]
         return out
 
     def sync(self, stream=None) -> None:

@@ -177,3 +177,27 @@ def test_invalid_stream_configs_are_rejected(bad):
     with pytest.raises(xcorr.XcorrError) as e:
         xcorr.Tracker(cfg(**bad), N_IN, N_CHAN)
     assert e.value.status == 1
+
+
+def test_packets_advance_moves_sequence_numbers_only():
+    pk = xcorr.xcorr_packetize(samples(BLOCK), cfg())
+    moved = pk.copy()
+    xcorr.xcorr_packets_advance(moved.ctypes.data, moved.shape[1], moved.shape[0], 12345)
+    seq0, fid0 = header(pk)
+    seq1, fid1 = header(moved)
+    assert np.array_equal(seq1, seq0 + 12345) and np.array_equal(fid1, fid0)
+    assert np.array_equal(moved[:, 8:], pk[:, 8:])
+
+
+def test_a_jump_past_the_event_buffer_still_progresses():
+    # a packet 50 blocks ahead needs 48 closes: with room for 5 events per call
+    # the tracker emits them over several calls and then places the packet
+    pk = xcorr.xcorr_packetize(samples(BLOCK), cfg())
+    far = pk[:1].copy()
+    xcorr.xcorr_packets_advance(far.ctypes.data, far.shape[1], 1, 50 * (BLOCK // NT) * N_GROUPS)
+    with xcorr.Tracker(cfg(n_blocks=2), N_IN, N_CHAN, max_events=5) as tr:
+        codes, ev = tr.feed(np.concatenate([pk[:3], far]))
+        closes = [e["block"] for e in ev if e["kind"] == xcorr.XCORR_EVENT_CLOSE]
+        assert closes == list(range(49))
+        assert codes[3] == ((50 % 2) << 40) | 0
+        assert tr.counters()["lost"] == 49 * P - 3

@@ -320,7 +320,7 @@ def test_every_launch_shape_is_exact(torch, variant, groups, x_streams):
     assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("n_sta,n_chan,n_time", [(8, 1, 1), (8, 2, 65), (64, 3, 300), (72, 2, 257),
                                                  (200, 2, 385), (256, 3, 1000)])
 def test_fused_4bit_kernel_bit_exact(torch, variant, n_sta, n_chan, n_time):
@@ -343,7 +343,7 @@ def test_fused_and_planes_paths_agree_over_several_executes(torch, unfused):
 FUSED_BLOCK = 37248  # samples per exactly-summed block of the fused kernel
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("pattern", ["max", "extremes"])
 def test_fused_exact_across_blocks_at_the_bound(torch, variant, pattern):
     # Two full blocks and a tail.  "max": every sample 7 + 7i, so each block's
@@ -480,3 +480,25 @@ def test_workload_512_inputs_512_channels_2048_samples(torch, workload_512, engi
     got, _ = run(torch, workload_512, engine)
     sample_check(got, workload_512, oracle.FMT_CI4, channels=[0, 137, 511], n_pairs_sample=400,
                  seed=3)
+
+
+@pytest.mark.parametrize("fmt,n_sta,n_chan,n_time,n_groups", [
+    ("ci4", 64, 13, 300, 0), ("ci4", 72, 9, 129, 4), ("ci4", 8, 3, 65, 8), ("ci4", 70, 4, 100, 0),
+    ("ci8", 32, 5, 200, 0)])
+def test_host_to_host_execute_matches_oracle(torch, fmt, n_sta, n_chan, n_time, n_groups):
+    # channel groups copied up, correlated and copied down in a pipeline (the
+    # fused 4-bit path); other inputs (70 stations: N_i not a multiple of 16,
+    # int8) take the one-piece path; either way the result is the oracle's
+    gen = synth.uniform_ci4 if fmt == "ci4" else synth.uniform_ci8
+    x = gen(n_time, n_chan, n_sta, seed=n_sta + n_time)
+    with xcorr.Plan(n_sta, n_chan, n_time, fmt=fmt) as plan:
+        xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        out = plan.execute_dump_host(xh, n_groups=n_groups)
+        plan.sync()
+        got = out.numpy().astype(np.int64)
+        # the plan holds nothing afterwards: a second call gives the same answer
+        out2 = plan.execute_dump_host(xh, n_groups=n_groups)
+        plan.sync()
+    want = oracle.correlate(oracle.FMT_CI4 if fmt == "ci4" else oracle.FMT_CI8, x)
+    assert np.array_equal(got, want)
+    assert np.array_equal(out2.numpy().astype(np.int64), want)
