@@ -595,9 +595,11 @@ def stream_arm(args) -> int:
     n_groups, n_feng = n_chan // w["nch"], n_in // w["na"]
     per_block = (block // w["nt"]) * n_groups * n_feng
     chunks_per_block = 8
+    # two blocks of landing chunks: a chunk whose scatter waits behind a long X
+    # launch does not hold up the next copies
     cfg = xcorr.stream_config(w["nt"], w["nch"], w["na"], block, n_blocks=4, blocks_per_dump=bpd,
                               stack_threshold=per_block // 4, chunk_packets=per_block // chunks_per_block,
-                              n_chunks=chunks_per_block, n_host_dumps=2)
+                              n_chunks=2 * chunks_per_block, n_host_dumps=2)
     xd = synth.gaussian_ci4_torch(block, n_chan, n_sta, seed=w["seed"] + info.rank)
     x = xd.cpu().numpy().reshape(block, n_chan, n_in)
     plan = xcorr.Plan(n_sta, n_chan, block)
@@ -612,8 +614,8 @@ def stream_arm(args) -> int:
     host_s = {"acquire": 0.0, "emulator": 0.0, "commit": 0.0}
 
     def push_block(b):
-        # chunk buffer k always carries the k-th eighth of a block: written whole
-        # once, then only moved one block ahead in time per reuse
+        # chunk buffer q always carries the (q mod 8)-th eighth of a block: written
+        # whole once, then only moved ahead in time by whole blocks per reuse
         for k in range(chunks_per_block):
             t0 = time.perf_counter()
             ptr, cap = stream.acquire()
