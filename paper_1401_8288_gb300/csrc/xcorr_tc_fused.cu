@@ -53,7 +53,6 @@ constexpr int kPrefetchSamples = 512;                   // L2 prefetch distance 
 // the TMA producer and the MMA warp.
 template <int DW>
 struct Roles {
-  static constexpr int kDecWarps = DW;
   static constexpr int kProducerWarp = kDecWarp0 + DW;
   static constexpr int kMmaWarp = kDecWarp0 + DW + 1;
   static constexpr int kThreads = (kDecWarp0 + DW + 2) * 32;
@@ -80,8 +79,6 @@ struct FGeom {
 };
 
 struct FParams {
-  const uint8_t* in;   // [t][c][i] CI4 bytes
-  int64_t row_stride;  // bytes from one sample to the next (n_chan * n_inputs)
   int n_chan, n_inputs, n_tile_pairs;
   int t0, t_end;       // samples [t0, t_end) of this launch
   int n_kt;            // stages per tile pair
@@ -550,8 +547,6 @@ cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int row_chans, int vari
       kFusedWindowCI4 % kt != 0)
     return cudaErrorInvalidValue;
   FParams p{};
-  p.in = in;
-  p.row_stride = (int64_t)row_chans * n_inputs;
   p.n_chan = n_chan;
   p.n_inputs = n_inputs;
   p.n_tile_pairs = nb * (nb + 1) / 2;
