@@ -462,6 +462,7 @@ xcorr_status xcorr_execute_dump_host(xcorr_plan plan, const void* h_in, int n_ti
   const size_t stage_bytes = row_bytes * plan->cfg.max_time_per_exec;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
+  // made on first use, each piece on its own so that a failed call leaves nothing half-made
   if (!plan->host_stage) {
     if ((e = cudaMalloc(&plan->host_stage, stage_bytes)) != cudaSuccess) {
       plan->host_stage = nullptr;
@@ -470,15 +471,23 @@ xcorr_status xcorr_execute_dump_host(xcorr_plan plan, const void* h_in, int n_ti
     }
     plan->host_stage_bytes = stage_bytes;
     plan->device_bytes += stage_bytes;
-    if ((e = cudaStreamCreateWithFlags(&plan->s_down, cudaStreamNonBlocking)) != cudaSuccess)
-      return cuda_fail(e, "stream create");
-    for (int g = 0; g < xc::kMaxGroups; ++g)
-      if ((e = cudaEventCreateWithFlags(&plan->ev_up[g], cudaEventDisableTiming)) != cudaSuccess ||
-          (e = cudaEventCreateWithFlags(&plan->ev_group_done[g], cudaEventDisableTiming)) != cudaSuccess)
-        return cuda_fail(e, "event create");
-    if ((e = cudaEventCreateWithFlags(&plan->ev_down, cudaEventDisableTiming)) != cudaSuccess)
-      return cuda_fail(e, "event create");
   }
+  if (!plan->s_down && (e = cudaStreamCreateWithFlags(&plan->s_down, cudaStreamNonBlocking)) != cudaSuccess) {
+    plan->s_down = nullptr;
+    return cuda_fail(e, "stream create");
+  }
+  for (cudaEvent_t* ev : {&plan->ev_down}) {
+    if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) {
+      *ev = nullptr;
+      return cuda_fail(e, "event create");
+    }
+  }
+  for (int g = 0; g < xc::kMaxGroups; ++g)
+    for (cudaEvent_t* ev : {&plan->ev_up[g], &plan->ev_group_done[g]})
+      if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) {
+        *ev = nullptr;
+        return cuda_fail(e, "event create");
+      }
   uint8_t* stage = static_cast<uint8_t*>(plan->host_stage);
   const size_t out_chan_bytes = static_cast<size_t>(plan->n_pairs) * 8;
   if (!(plan->engine == XCORR_ENGINE_TENSOR && fused_applies(plan, stage))) {

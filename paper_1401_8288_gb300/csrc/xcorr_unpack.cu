@@ -22,17 +22,20 @@ namespace {
 
 // Channels [c0, c0 + nc) of every time row, 16 inputs per thread (N_i a
 // multiple of 16 and a 16-byte aligned input); grid-stride over the rows.
+// Idx is the type of the flat index: 32-bit whenever the work fits, since the
+// two divisions per 16 bytes cost several times more in 64-bit arithmetic.
+template <typename Idx>
 __global__ void __launch_bounds__(256) unpack_ci4_e4m3_vec(const uint8_t* __restrict__ in,
                                                            uint8_t* __restrict__ planes, int64_t n_rows,
                                                            int n_chan, int c0, int nc, int q_per_row,
                                                            int ni_pad, int64_t comp_stride) {
-  const int64_t total = n_rows * q_per_row;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = q / q_per_row;  // row = t * nc + (c - c0)
+  const Idx total = static_cast<Idx>(n_rows * q_per_row);
+  for (Idx q = blockIdx.x * static_cast<Idx>(blockDim.x) + threadIdx.x; q < total;
+       q += static_cast<Idx>(gridDim.x) * blockDim.x) {
+    const Idx row = q / static_cast<Idx>(q_per_row);  // row = t * nc + (c - c0)
     const int k = static_cast<int>(q - row * q_per_row);
-    const int64_t t = row / nc;
-    const int c = c0 + static_cast<int>(row - t * nc);
+    const int64_t t = static_cast<int64_t>(row / static_cast<Idx>(nc));
+    const int c = c0 + static_cast<int>(row - static_cast<Idx>(t) * nc);
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + ((t * n_chan + c) * q_per_row + k) * 16));
     uint4 r, m;
     ci4_to_e4m3(v.x, r.x, m.x);
@@ -79,9 +82,13 @@ cudaError_t launch_unpack_ci4_e4m3_channels(const uint8_t* in, uint8_t* planes, 
   const int64_t cap = (int64_t)num_sms * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  if (vec)
-    unpack_ci4_e4m3_vec<<<(unsigned)blocks, threads, 0, stream>>>(in, planes, n_rows, n_chan, c0, nc,
-                                                                 n_inputs / 16, ni_pad, comp_stride);
+  const bool idx32 = work + (int64_t)blocks * threads < (INT64_C(1) << 32);
+  if (vec && idx32)
+    unpack_ci4_e4m3_vec<uint32_t><<<(unsigned)blocks, threads, 0, stream>>>(in, planes, n_rows, n_chan, c0, nc,
+                                                                           n_inputs / 16, ni_pad, comp_stride);
+  else if (vec)
+    unpack_ci4_e4m3_vec<int64_t><<<(unsigned)blocks, threads, 0, stream>>>(in, planes, n_rows, n_chan, c0, nc,
+                                                                          n_inputs / 16, ni_pad, comp_stride);
   else
     unpack_ci4_e4m3_byte<<<(unsigned)blocks, threads, 0, stream>>>(in, planes, n_rows, n_chan, c0, nc,
                                                                   n_inputs, ni_pad, comp_stride);
@@ -165,17 +172,19 @@ __device__ __forceinline__ uint32_t bf16_bits(float f) {
 
 // Eight int8 samples (16 bytes: re, im interleaved) -> eight BF16 real parts
 // and eight imaginary parts, exact (|v| <= 128 needs 8 significant bits).
+// Idx as for unpack_ci4_e4m3_vec.
+template <typename Idx>
 __global__ void __launch_bounds__(256) unpack_ci8_bf16_vec(const int8_t* __restrict__ in,
                                                            uint16_t* __restrict__ planes, int64_t n_rows,
                                                            int n_chan, int c0, int nc, int q_per_row,
                                                            int ni_pad, int64_t comp_stride) {
-  const int64_t total = n_rows * q_per_row;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = q / q_per_row;
+  const Idx total = static_cast<Idx>(n_rows * q_per_row);
+  for (Idx q = blockIdx.x * static_cast<Idx>(blockDim.x) + threadIdx.x; q < total;
+       q += static_cast<Idx>(gridDim.x) * blockDim.x) {
+    const Idx row = q / static_cast<Idx>(q_per_row);
     const int k = static_cast<int>(q - row * q_per_row);
-    const int64_t t = row / nc;
-    const int c = c0 + static_cast<int>(row - t * nc);
+    const int64_t t = static_cast<int64_t>(row / static_cast<Idx>(nc));
+    const int c = c0 + static_cast<int>(row - static_cast<Idx>(t) * nc);
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + ((t * n_chan + c) * q_per_row + k) * 16));
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
     uint32_t re[4], im[4];
@@ -287,9 +296,13 @@ cudaError_t launch_unpack_ci8_bf16(const int8_t* in, uint16_t* planes, int n_tim
   const int64_t n_rows = (int64_t)n_time * nc;
   const int64_t comp_stride = (int64_t)max_time * ni_pad;
   const bool vec = (n_inputs % 8 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0);
-  if (vec)
-    unpack_ci8_bf16_vec<<<(unsigned)grid_for(n_rows * (n_inputs / 8), num_sms), 256, 0, stream>>>(
-        in, planes, n_rows, n_chan, c0, nc, n_inputs / 8, ni_pad, comp_stride);
+  const int64_t work = n_rows * (n_inputs / 8), blocks = grid_for(work, num_sms);
+  if (vec && work + blocks * 256 < (INT64_C(1) << 32))
+    unpack_ci8_bf16_vec<uint32_t><<<(unsigned)blocks, 256, 0, stream>>>(in, planes, n_rows, n_chan, c0, nc,
+                                                                       n_inputs / 8, ni_pad, comp_stride);
+  else if (vec)
+    unpack_ci8_bf16_vec<int64_t><<<(unsigned)blocks, 256, 0, stream>>>(in, planes, n_rows, n_chan, c0, nc,
+                                                                      n_inputs / 8, ni_pad, comp_stride);
   else
     unpack_ci8_bf16_elem<<<(unsigned)grid_for(n_rows * n_inputs, num_sms), 256, 0, stream>>>(
         in, planes, n_rows, n_chan, c0, nc, n_inputs, ni_pad, comp_stride);

@@ -157,3 +157,22 @@ def test_budget_admission(torch):
         with pytest.raises(xcorr.XcorrError) as e:
             xcorr.Stream(plan, cfg())
         assert e.value.status == 7  # BUDGET
+
+
+@pytest.mark.parametrize("nt,nch,na,engine", [(2, 16, 32, "tensor"), (1, 4, 64, "cuda_core"),
+                                              (8, 2, 16, "tensor")])
+def test_other_packet_geometries(torch, nt, nch, na, engine):
+    # spectra per packet, channels per packet and F-engine widths other than the
+    # defaults; chunks of 37 packets split packets of a block across chunks
+    n_blocks = 3
+    x = synth.uniform_ci4(n_blocks * BLOCK, N_CHAN, N_STA, seed=nt * 100 + na, lo=-8, hi=7).reshape(-1, N_CHAN, N_IN)
+    c = cfg(n_time_per_packet=nt, n_chan_per_packet=nch, n_inputs_per_packet=na, blocks_per_dump=3,
+            chunk_packets=37, n_chunks=2)
+    pk = xcorr.xcorr_packetize(x, c)
+    rng = np.random.default_rng(nt + na)
+    order = np.argsort(np.arange(pk.shape[0]) + rng.uniform(0, 20, pk.shape[0]))
+    dumps, counters = run_stream(torch, x, pk[order], c, engine)
+    assert counters["lost"] == 0 and counters["placed"] == pk.shape[0]
+    assert len(dumps) == 1 and dumps[0]["n_samples"] == n_blocks * BLOCK
+    want = oracle.correlate(oracle.FMT_CI4, x.reshape(-1, N_CHAN, N_STA, 2))
+    assert np.array_equal(dumps[0]["data"].astype(np.int64), want)
