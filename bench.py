@@ -254,6 +254,10 @@ def reference_arm(args) -> int:
         emit({"impl": "reference", "unavailable": "the oracle arm times single workloads; "
               "run it per subarray size"})
         return 0
+    if args.workload == "stream1024":
+        emit({"impl": "reference", "unavailable": "the oracle has no packet path; its correlation "
+              "rate is the reference line of the default workload"})
+        return 0
     w = WORKLOADS[args.workload]
     x = make_input(w, w["seed"])
     ofmt = {"ci4": oracle.FMT_CI4, "ci8": oracle.FMT_CI8, "cf32": oracle.FMT_CF32}[w["fmt"]]
