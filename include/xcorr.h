@@ -199,6 +199,18 @@ xcorr_status xcorr_execute_dump_host(xcorr_plan plan, const void *h_in, int n_ti
 xcorr_status xcorr_sync(xcorr_plan plan, void *stream);
 
 /*
+ * Check the failure path of the kernels' bounded waits.  This enqueues one
+ * kernel whose wait can never complete: an mbarrier that nothing arrives at.
+ * The wait gives up after the library's wait limit (2 s) and records a
+ * timeout in the plan's status word, exactly as a stalled X-stage kernel
+ * would.  The next xcorr_sync then returns XCORR_ERR_DEVICE, and the plan
+ * refuses every later call until xcorr_destroy.  No GPU fault is involved,
+ * and other plans on the device keep working.  Errors: INVALID_ARG, CUDA,
+ * DEVICE.
+ */
+xcorr_status xcorr_watchdog_selftest(xcorr_plan plan, void *stream);
+
+/*
  * Fix the tensor path's launch shape (results do not depend on it).
  * Errors: INVALID_ARG (stage_variant not in [0, 3], groups not in [0, 8],
  * x_streams not 1 or 2), DEVICE.

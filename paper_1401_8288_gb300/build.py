@@ -9,6 +9,8 @@ header or this file is newer than its object.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import contextlib
+import fcntl
 import glob
 import os
 import shutil
@@ -44,10 +46,27 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+@contextlib.contextmanager
+def _build_lock():
+    """One build at a time: ranks launched together (torchrun) all call build(),
+    and the first does the work while the others wait and find it done."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    with open(os.path.join(OUT_DIR, ".build.lock"), "w") as fh:
+        fcntl.flock(fh, fcntl.LOCK_EX)
+        try:
+            yield
+        finally:
+            fcntl.flock(fh, fcntl.LOCK_UN)
+
+
 def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     """Compile every translation unit and link the library; returns its path."""
+    with _build_lock():
+        return _build(verbose, extra_flags)
+
+
+def _build(verbose: bool, extra_flags: list[str] | None) -> str:
     nvcc = _nvcc()
-    os.makedirs(OUT_DIR, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     headers = _headers()
     flags = FLAGS + (extra_flags or [])

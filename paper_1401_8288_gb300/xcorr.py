@@ -37,7 +37,8 @@ EXPORTS = ("xcorr_plan_create", "xcorr_execute", "xcorr_dump", "xcorr_sync", "xc
            "xcorr_tracker_destroy", "xcorr_packetize", "xcorr_stream_create", "xcorr_stream_acquire",
            "xcorr_stream_commit", "xcorr_stream_flush", "xcorr_stream_counters",
            "xcorr_stream_wait_dump", "xcorr_stream_destroy", "xcorr_packets_advance",
-           "xcorr_execute_dump_host", "xcorr_bdi_create", "xcorr_bdi_step", "xcorr_bdi_destroy")
+           "xcorr_execute_dump_host", "xcorr_bdi_create", "xcorr_bdi_step", "xcorr_bdi_destroy",
+           "xcorr_watchdog_selftest")
 XCORR_PACKET_HEADER_BYTES = 16
 XCORR_EVENT_OPEN, XCORR_EVENT_CLOSE = 1, 2
 PEAK_KINDS = {"tc_e4m3": 0, "tc_bf16": 1, "mma_sync_s8": 2, "dp4a": 3}
@@ -159,6 +160,7 @@ def load():
                 "xcorr_bdi_step": [vp, vp, i, vp, ctypes.POINTER(i), ctypes.POINTER(i),
                                    ctypes.POINTER(i64)],
                 "xcorr_bdi_destroy": [vp],
+                "xcorr_watchdog_selftest": [vp, vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -210,6 +212,10 @@ def xcorr_execute_dump(plan, d_in: int, n_time: int, out: int, out_on_device: bo
 def xcorr_execute_dump_host(plan, h_in: int, n_time: int, h_out: int, n_groups: int = 0,
                             stream: int = 0) -> None:
     _check(load().xcorr_execute_dump_host(plan, h_in, n_time, h_out, n_groups, stream))
+
+
+def xcorr_watchdog_selftest(plan, stream: int = 0) -> None:
+    _check(load().xcorr_watchdog_selftest(plan, stream))
 
 
 def xcorr_sync(plan, stream: int = 0) -> None:

@@ -525,3 +525,23 @@ def test_host_to_host_execute_matches_oracle(torch, fmt, n_sta, n_chan, n_time, 
     want = oracle.correlate(oracle.FMT_CI4 if fmt == "ci4" else oracle.FMT_CI8, x)
     assert np.array_equal(got, want)
     assert np.array_equal(out2.numpy().astype(np.int64), want)
+
+
+def test_a_stalled_wait_is_reported_and_the_context_survives(torch):
+    # a wait that can never complete gives up after the 2 s limit and turns the
+    # plan's status to DEVICE; nothing faults, and a new plan works as before
+    import time
+    x = synth.uniform_ci4(16, 1, 8, seed=9, lo=-8, hi=7)
+    xd = torch.from_numpy(x).cuda()
+    with xcorr.Plan(8, 1, 16) as plan:
+        t0 = time.perf_counter()
+        xcorr.xcorr_watchdog_selftest(plan.handle, 0)
+        with pytest.raises(xcorr.XcorrError) as e:
+            plan.sync(0)
+        assert e.value.status == 6
+        assert time.perf_counter() - t0 > 1.0
+        with pytest.raises(xcorr.XcorrError) as e:
+            plan.execute(xd)  # the plan refuses work until destroyed
+        assert e.value.status == 6
+    got, _ = run(torch, x, "tensor")
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
