@@ -90,14 +90,17 @@ typedef struct xcorr_plan_s *xcorr_plan;
 
 /* Launch shape of the tensor-core path (xcorr_plan_set_tuning, xcorr_autotune). */
 typedef struct {
-    int stage_variant;  /* shared-memory ring, 0 .. 3: planes path 0 = 3 x 64 KB, 1 (and 3) =
-                           4 x 48 KB, 2 = 6 x 32 KB stages; fused path see `unfused`           */
+    int stage_variant;  /* shared-memory ring, 0 .. 6: planes path 0 = 3 x 64 KB, 1 (and 3 .. 6)
+                           = 4 x 48 KB, 2 = 6 x 32 KB stages; fused path see `unfused`         */
     int groups;         /* channel groups whose unpack overlaps the X kernel; 0 = automatic (<= 8) */
     int x_streams;      /* 1 or 2 streams the groups' X launches alternate over                 */
     int unfused;        /* 4-bit input: 0 = unpack on chip inside the X kernel where possible
                            (N_i % 16 == 0, 16-byte aligned input); stage_variant then picks
                            raw / decoded rings of 128 x (2 + 2), 96 x (4 + 2), 64 x (6 + 3)
-                           samples with 8 decoder warps, or 96 x (4 + 2) with 12;
+                           samples with 8 decoder warps, or 96 x (4 + 2) with 12 (both
+                           operands decoded into shared memory); 4 .. 6: the A operand
+                           decoded into tensor memory, raw / decoded rings of
+                           64 x (2 + 3), 32 x (4 + 6), 64 x (3 + 2) samples;
                            1 = always through E4M3 planes in HBM                            */
 } xcorr_tuning;
 
@@ -212,7 +215,7 @@ xcorr_status xcorr_watchdog_selftest(xcorr_plan plan, void *stream);
 
 /*
  * Fix the tensor path's launch shape (results do not depend on it).
- * Errors: INVALID_ARG (stage_variant not in [0, 3], groups not in [0, 8],
+ * Errors: INVALID_ARG (stage_variant not in [0, 6], groups not in [0, 8],
  * x_streams not 1 or 2), DEVICE.
  */
 xcorr_status xcorr_plan_set_tuning(xcorr_plan plan, const xcorr_tuning *tuning);

@@ -139,6 +139,39 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 16 lanes x 128 bits: thread t of the warp writes r0 to lane lane0 + t / 4 and
+// r1 to lane lane0 + 8 + t / 4, both at column col + t % 4 of the address.
+__device__ __forceinline__ void tmem_st_16x128b(uint32_t taddr, uint32_t r0, uint32_t r1) {
+  asm volatile("tcgen05.st.sync.aligned.16x128b.x1.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(r0), "r"(r1)
+               : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns, the inverse of tmem_ld16.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// -------------------------------------------------------------- ldmatrix --
+// A 16 x 16 byte matrix, transposed: threads 0-15 give the addresses of rows
+// 0-15 (16 bytes each); thread t receives rows 4 (t % 4) .. 4 (t % 4) + 3 of
+// column t / 4 in d0 (row order from the low byte up) and of column t / 4 + 8
+// in d1.
+__device__ __forceinline__ void ldmatrix_t_b8(uint32_t saddr, uint32_t& d0, uint32_t& d1) {
+  asm volatile("ldmatrix.sync.aligned.m16n16.x1.trans.shared.b8 {%0, %1}, [%2];"
+               : "=r"(d0), "=r"(d1)
+               : "r"(saddr)
+               : "memory");
+}
+
 // ------------------------------------------------------------------ tcgen05 --
 // Shared-memory matrix descriptor, 128-byte swizzle.  For an MN-major operand
 // `lbo` is the byte distance between 128-byte-wide chunks along M/N and `sbo`
@@ -159,6 +192,12 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_type, bool mn_majo
          (mn_major ? ((1u << 15) | (1u << 16)) : 0u) | (static_cast<uint32_t>(n >> 3) << 17) |
          (static_cast<uint32_t>(m >> 4) << 24);
 }
+// As instr_desc with A K-major (as it must be when it is read from tensor
+// memory) and B MN-major.
+__host__ __device__ constexpr uint32_t instr_desc_ta(uint32_t ab_type, int m, int n, bool negate_a) {
+  return (1u << 4) | (ab_type << 7) | (ab_type << 10) | (negate_a ? (1u << 13) : 0u) | (1u << 16) |
+         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
+}
 constexpr uint32_t kTypeE4M3 = 0;  // kind::f8f6f4
 constexpr uint32_t kTypeF16 = 0;   // kind::f16
 constexpr uint32_t kTypeBF16 = 1;  // kind::f16
@@ -169,6 +208,16 @@ __device__ __forceinline__ void mma_f8f6f4(uint32_t d_tmem, uint64_t a_desc, uin
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
+// As mma_f8f6f4 with the A operand in tensor memory: lane m holds row m, and
+// column c holds K elements 4c .. 4c + 3 from the low byte up.
+__device__ __forceinline__ void mma_f8f6f4_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,

@@ -583,7 +583,7 @@ xcorr_status xcorr_plan_set_tuning(xcorr_plan plan, const xcorr_tuning* t) {
   if (st != XCORR_OK) return st;
   if (!t) return fail(XCORR_ERR_INVALID_ARG, "tuning is NULL");
   if (t->stage_variant < 0 || t->stage_variant >= xc::kFusedVariants)
-    return fail(XCORR_ERR_INVALID_ARG, "stage_variant must be in [0, 3]");
+    return fail(XCORR_ERR_INVALID_ARG, "stage_variant must be in [0, " + std::to_string(xc::kFusedVariants - 1) + "]");
   if (t->groups < 0 || t->groups > xc::kMaxGroups) return fail(XCORR_ERR_INVALID_ARG, "groups must be in [0, 8]");
   if (t->x_streams != 1 && t->x_streams != 2) return fail(XCORR_ERR_INVALID_ARG, "x_streams must be 1 or 2");
   if (t->unfused != 0 && t->unfused != 1) return fail(XCORR_ERR_INVALID_ARG, "unfused must be 0 or 1");

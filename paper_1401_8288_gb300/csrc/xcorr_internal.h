@@ -31,7 +31,7 @@ constexpr int kTcWindowBF16 = 384;
 // stays below 2^24 for T <= 37,282; rounded down to a multiple of 384 (every stage height).
 constexpr int kFusedWindowCI4 = 37248;
 constexpr int kTcVariants = 3;     // planes-path stage shapes: 64 KB x 3, 48 KB x 4, 32 KB x 6
-constexpr int kFusedVariants = 4;  // fused 4-bit kernel shapes (the tuning's stage_variant range)
+constexpr int kFusedVariants = 7;  // fused 4-bit kernel shapes (the tuning's stage_variant range)
 // The planes path's shape for a tuning's stage_variant (3 exists only for the fused kernel).
 inline int planes_variant(int v) { return v >= kTcVariants ? 1 : v; }
 constexpr int64_t kMaxIntegrationCF32 = INT64_C(16777216);  // FP32 per dump, widen beyond
@@ -187,9 +187,16 @@ bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_c
 int fused_stage_samples(int variant);
 int fused_launches(int n_time);
 // `in` points at the first of n_chan channels; time rows hold row_chans channels.
+// Variants 0-3 decode both operands into shared memory; 4-6 run the kernel
+// with the A operand in tensor memory (its variants 0-2).
 cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                       int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
                                       cudaStream_t stream);
+
+int fused_ta_stage_samples(int variant);
+cudaError_t launch_xcorr_tc_fused_ta_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
+                                         int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
+                                         cudaStream_t stream);
 
 // int8 (re, im) samples -> two BF16 planes [c][2][t][ni_pad] (exact).
 cudaError_t launch_unpack_ci8_bf16(const int8_t* in, uint16_t* planes, int n_time, int n_chan, int c0,

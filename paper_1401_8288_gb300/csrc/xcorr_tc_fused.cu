@@ -29,13 +29,15 @@
 // sum; warp 12 is the TMA producer (and prefetches into L2 further ahead);
 // warp 13 allocates TMEM and issues the three MMAs per 32-sample step into
 // [Re | -Im] (double-buffered).  Every wait is bounded (sm103_ptx.cuh).
+#include "fused_common.cuh"
 #include "sm103_ptx.cuh"
 #include "xcorr_internal.h"
 
 namespace xc {
 namespace {
 
-constexpr int kBlk = 128;
+using namespace fused;
+
 constexpr int kEpiWarps = 4;
 constexpr int kDecWarp0 = 4;
 constexpr int kChunk = 16;
@@ -43,11 +45,14 @@ constexpr int kPitch = kChunk + 1;
 constexpr int kAccCols = 256;  // [Re | -Im]
 constexpr uint32_t kTmemCols = 512;
 constexpr int kStagingBytes = kEpiWarps * 32 * kPitch * 8;
-constexpr int kSumsBytes = 2 * 2 * kBlk * 8;            // [TMEM buffer][I, J][input] (P, Q)
+constexpr int kSumsBytes = 2 * 2 * kBlk * 8;            // [TMEM buffer][I, J][input] (8P, 8Q)
+// Every partial sum of u_a u_b is n 2^-18 with 0 <= n <= 450 T (and |n| <= 225 T for Im).
+// For T <= kMagicSamples, |n| < 2^22 and n + 1.5 2^23 is exact in FP32, so one FFMA
+// against that constant turns the accumulator into n (in the low bits of the result).
+constexpr int kMagicSamples = 9320;
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
 constexpr int kBarrierBytes = 256;
-constexpr uint32_t kNibbleTop = 0x88888888u;            // t -> t + 8 on every nibble
-constexpr uint32_t kLowNibbles = 0x0F0F0F0Fu;
-constexpr int kPrefetchSamples = 512;                   // L2 prefetch distance along time
 
 // Warp roles for DW decoder warps: 0-3 epilogue, 4 .. 3 + DW decoders, then
 // the TMA producer and the MMA warp.
@@ -88,77 +93,6 @@ struct FParams {
   int* status;
   uint32_t one;        // 1: a multiplier the compiler cannot fold (see lane_add)
 };
-
-__device__ __forceinline__ void tile_pair(int p, int& I, int& J) {
-  int i = static_cast<int>((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
-  while ((i + 1) * (i + 2) / 2 <= p) ++i;
-  while (i * (i + 1) / 2 > p) --i;
-  I = i;
-  J = p - i * (i + 1) / 2;
-}
-
-
-// L2 prefetch of one TMA box (no shared memory, nothing to wait for).
-__device__ __forceinline__ void tma_prefetch_3d(const void* tmap, int x, int y, int z) {
-  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
-                   reinterpret_cast<uint64_t>(tmap)),
-               "r"(x), "r"(y), "r"(z)
-               : "memory");
-}
-
-// A tile pair of the CTA's item list.
-struct Item {
-  int c, I, J;
-  bool diag, valid;
-};
-
-__device__ __forceinline__ Item item_at(const FParams& p, int item, int n_items) {
-  Item it{};
-  it.valid = item < n_items;
-  if (it.valid) {
-    it.c = item / p.n_tile_pairs;
-    tile_pair(item - it.c * p.n_tile_pairs, it.I, it.J);
-    it.diag = it.I == it.J;
-  }
-  return it;
-}
-
-// L2 prefetch of stage s of an item: one box per tile (128 inputs x KT samples).
-template <int KT>
-__device__ __forceinline__ void prefetch_stage(const CUtensorMap* raw_map, const FParams& p, const Item& it, int s) {
-  if (!it.valid || s >= p.n_kt) return;
-  const int t = p.t0 + s * KT;
-  tma_prefetch_3d(raw_map, it.I * kBlk, it.c, t);
-  if (!it.diag) tma_prefetch_3d(raw_map, it.J * kBlk, it.c, t);
-}
-
-// The decoder warps' own barrier (id 1), and its OR-reduction form.
-__device__ __forceinline__ void dec_bar_sync(uint32_t n_threads) {
-  asm volatile("bar.sync 1, %0;" ::"r"(n_threads) : "memory");
-}
-__device__ __forceinline__ bool dec_bar_or(bool v, uint32_t n_threads) {
-  uint32_t r;
-  asm volatile(
-      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, 1, %2, q;\nselp.u32 %0, 1, 0, p;\n}"
-      : "=r"(r)
-      : "r"(static_cast<uint32_t>(v)), "r"(n_threads)
-      : "memory");
-  return r != 0;
-}
-
-// a += b as an integer multiply-add by `one` (== 1 at run time).  The decoders'
-// byte-lane sums then issue on the FMA pipe instead of the ALU pipe, which the
-// decode itself keeps busy.
-__device__ __forceinline__ void lane_add(uint32_t& a, uint32_t b, uint32_t one) {
-  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(a) : "r"(b), "r"(one));
-}
-
-// Four CI4 bytes -> four offset E4M3 real codes and four imaginary codes.
-__device__ __forceinline__ void offset_codes(uint32_t w, uint32_t& re, uint32_t& im) {
-  const uint32_t u = w ^ kNibbleTop;
-  im = u & kLowNibbles;
-  re = (u >> 4) & kLowNibbles;
-}
 
 // One decoder thread's share of one tile pair: a fixed 16-input chunk L of one
 // tile and rows phase, phase + KT/R, ...; R rows per stage.  A raw chunk sits
@@ -285,19 +219,20 @@ __global__ void __launch_bounds__(Roles<DW>::kThreads, 1)
       constexpr int kAhead = kPrefetchSamples / KT;  // L2 prefetch runs this many stages ahead of the loads
       prefetch_tmap(&raw_map);
       {
-        const Item first = item_at(p, blockIdx.x, n_items);
-        for (int s = 0; s < kAhead; ++s) prefetch_stage<KT>(&raw_map, p, first, s);
+        const Item first = item_at(p.n_tile_pairs, blockIdx.x, n_items);
+        for (int s = 0; s < kAhead; ++s) prefetch_stage<KT>(&raw_map, p.t0, p.n_kt, first, s);
       }
       int r = 0;
       uint32_t ph = 0, filled = 0, fill_parity[RAW] = {};
       bool ok = true;
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-        const Item it = item_at(p, item, n_items);
+        const Item it = item_at(p.n_tile_pairs, item, n_items);
         for (int tb = 0; tb < p.n_kt; ++tb) {
           if (tb + kAhead < p.n_kt)
-            prefetch_stage<KT>(&raw_map, p, it, tb + kAhead);
+            prefetch_stage<KT>(&raw_map, p.t0, p.n_kt, it, tb + kAhead);
           else
-            prefetch_stage<KT>(&raw_map, p, item_at(p, item + gridDim.x, n_items), tb + kAhead - p.n_kt);
+            prefetch_stage<KT>(&raw_map, p.t0, p.n_kt, item_at(p.n_tile_pairs, item + gridDim.x, n_items),
+                               tb + kAhead - p.n_kt);
           if (!mbar_wait(&raw_empty[r], ph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
             ok = false;
             break;
@@ -326,7 +261,7 @@ __global__ void __launch_bounds__(Roles<DW>::kThreads, 1)
     int r = 0, d = 0, g = 0;
     uint32_t rph = 0, dph = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
-      const Item cur = item_at(p, item, n_items);
+      const Item cur = item_at(p.n_tile_pairs, item, n_items);
       const bool diag = cur.diag;
       uint32_t s_re[8], s_im[8];
       // off the diagonal the first half of the threads take tile I and the second half tile J;
@@ -372,7 +307,7 @@ __global__ void __launch_bounds__(Roles<DW>::kThreads, 1)
           s.x += x.x;
           s.y += x.y;
         }
-        sums[(buf * 2 + slot) * kBlk + e] = s;
+        sums[(buf * 2 + slot) * kBlk + e] = make_int2(8 * s.x, 8 * s.y);
       }
       if (dec_bar_or(!ok || *abort_flag, W::kDecThreads)) break;
       if (tid == 0) mbar_arrive(&sfull[buf]);
@@ -450,49 +385,57 @@ __global__ void __launch_bounds__(Roles<DW>::kThreads, 1)
           !mbar_wait_warp(&sfull[buf], use & 1u, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL))
         break;
       tc_fence_after();
-      const int2 rs = sums[(buf * 2) * kBlk + warp * 32 + lane];
-      const int2* cs = sums + (buf * 2 + (I == J ? 0 : 1)) * kBlk;
+      const int2 rs = sums[(buf * 2) * kBlk + warp * 32 + lane];  // (8P, 8Q) of this row's input
+      const int4* cs4 = reinterpret_cast<const int4*>(sums + (buf * 2 + (I == J ? 0 : 1)) * kBlk);
+      const bool magic = t128 <= 128 * kMagicSamples;
+      // Re = n_re - 8 P_a - 8 P_b + 128 T,  Im = -n_im - 8 Q_a + 8 Q_b
+      const int row_re = t128 - rs.x - (magic ? kMagicBits : 0);
+      const int row_im = -rs.y + (magic ? kMagicBits : 0);
       const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + buf * kAccCols;
       for (int j0 = 0; j0 < kBlk; j0 += kChunk) {
+        const int jfirst = J * kBlk + j0;
+        if (jfirst > row0 + 31 || row0 >= p.n_inputs) continue;  // wholly above the diagonal or past the inputs
         uint32_t re[16], nim[16];
         tmem_ld16(taddr + j0, re);
         tmem_ld16(taddr + 128 + j0, nim);
+        // the column sums first: the staging stores below would otherwise hold back every load
+        int4 s[kChunk / 2];
+#pragma unroll
+        for (int k = 0; k < kChunk / 2; ++k) s[k] = cs4[j0 / 2 + k];  // (8P, 8Q) of columns 2k, 2k + 1
         tmem_ld_wait();
-        const int jfirst = J * kBlk + j0;
-        if (jfirst > row0 + 31 || row0 >= p.n_inputs) continue;  // wholly above the diagonal or past the inputs
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const int2 s = cs[j0 + q];
-          const int re_u = __float2int_rn(__uint_as_float(re[q]) * 262144.0f);  // sums of u_a u_b
-          const int nim_u = __float2int_rn(__uint_as_float(nim[q]) * 262144.0f);
-          stage_rows[lane * kPitch + q] = make_int2(re_u - 8 * (rs.x + s.x) + t128, -nim_u - 8 * rs.y + 8 * s.y);
+          re[q] = magic ? __float_as_uint(fmaf(__uint_as_float(re[q]), 262144.0f, kMagic))
+                        : static_cast<uint32_t>(__float2int_rn(__uint_as_float(re[q]) * 262144.0f));
+          nim[q] = magic ? __float_as_uint(fmaf(__uint_as_float(nim[q]), 262144.0f, kMagic))
+                         : static_cast<uint32_t>(__float2int_rn(__uint_as_float(nim[q]) * 262144.0f));
+        }
+#pragma unroll
+        for (int k = 0; k < kChunk / 2; ++k) {
+          stage_rows[lane * kPitch + 2 * k] =
+              make_int2(static_cast<int>(re[2 * k]) + row_re - s[k].x, -static_cast<int>(nim[2 * k]) + row_im + s[k].y);
+          stage_rows[lane * kPitch + 2 * k + 1] = make_int2(static_cast<int>(re[2 * k + 1]) + row_re - s[k].z,
+                                                            -static_cast<int>(nim[2 * k + 1]) + row_im + s[k].w);
         }
         __syncwarp();
-        // a half-warp writes 16 consecutive pairs of one row
+        // a half-warp writes 16 consecutive pairs of one row: the 16 staged values first, then the stores
         const int j = jfirst + col;
-        uint32_t valid = 0;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int i = row0 + 2 * r + half;
-          if (i < p.n_inputs && j <= i) valid |= 1u << r;
-        }
-        // 8 rows at a time; when the integration continues, all 8 loads go out before the adds
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          int2 old[8];
+          int2 v[8];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) v[r] = stage_rows[(2 * (8 * h + r) + half) * kPitch + col];
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
-            const int rh = 8 * h + r, i = row0 + 2 * rh + half;
-            old[r] = (p.accumulate && ((valid >> rh) & 1u)) ? out_c[(int64_t)i * (i + 1) / 2 + j] : make_int2(0, 0);
-          }
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int rh = 8 * h + r;
-            if ((valid >> rh) & 1u) {
-              const int rr = 2 * rh + half;
-              const int i = row0 + rr;
-              const int2 v = stage_rows[rr * kPitch + col];
-              out_c[(int64_t)i * (i + 1) / 2 + j] = make_int2(v.x + old[r].x, v.y + old[r].y);
+            const int i = row0 + 2 * (8 * h + r) + half;
+            if (i < p.n_inputs && j <= i) {
+              int2* dst = out_c + (int64_t)i * (i + 1) / 2 + j;
+              if (p.accumulate) {
+                const int2 o = *dst;
+                v[r].x += o.x;
+                v[r].y += o.y;
+              }
+              *dst = v[r];
             }
           }
         }
@@ -532,15 +475,22 @@ cudaError_t launch_fused(const CUtensorMap& raw_map, const FParams& p, int grid,
 }  // namespace
 
 // The fused variants: 128 samples (2 raw + 2 decoded stages), 96 (4 + 2), 64 (6 + 3), all with
-// 8 decoder warps, and 96 (4 + 2) with 12.  Deeper raw rings hide more TMA latency, deeper
+// 8 decoder warps, and 96 (4 + 2) with 12; variants 4-6 are the kernel of xcorr_tc_fused_ta.cu
+// (A operand in tensor memory).  Deeper raw rings hide more TMA latency, deeper
 // decoded rings more decoder jitter, more decoder warps more of the decode's latency.
-int fused_stage_samples(int variant) { return variant == 0 ? 128 : variant == 2 ? 64 : 96; }
+int fused_stage_samples(int variant) {
+  if (variant >= 4) return fused_ta_stage_samples(variant - 4);
+  return variant == 0 ? 128 : variant == 2 ? 64 : 96;
+}
 
 int fused_launches(int n_time) { return n_time <= 0 ? 0 : (n_time + kFusedWindowCI4 - 1) / kFusedWindowCI4; }
 
 cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                       int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
                                       cudaStream_t stream) {
+  if (variant >= 4)
+    return launch_xcorr_tc_fused_ta_ci4(in, row_chans, variant - 4, n_time, n_chan, n_inputs, out, accumulate, status,
+                                        num_sms, stream);
   const int nb = (n_inputs + kBlk - 1) / kBlk;
   const int kt = fused_stage_samples(variant);
   if (n_time <= 0 || n_inputs % 16 != 0 || reinterpret_cast<uintptr_t>(in) % 16 != 0 ||

@@ -1,0 +1,571 @@
+// xcorr_tc_fused_ta.cu -- the fused 4-bit X-stage with the A operand decoded
+// straight into tensor memory.
+//
+// Same result as xcorr_tc_fused.cu (per channel, the packed lower triangle of
+// V = sum_t x_t x_t^H; Sec. 1, Sec. 2.1, Eq. 1) from the same raw [t][c][i]
+// CI4 bytes and the same offset-binary E4M3 operands u = t + 8, but the row
+// tile's operand never goes through shared memory.  In the shared-memory
+// kernel every MMA re-reads A from shared memory, and the operand reads, the
+// decoders' stores and the TMA writes together exhaust the SM's shared-memory
+// bandwidth well before the tensor pipe; here A lives in tensor memory:
+//
+//   * one ldmatrix.trans of a 16-sample x 16-input block of raw bytes gives
+//     each thread four consecutive samples of one input, which is exactly the
+//     register layout a tcgen05.st of 16 lanes x 128 bits takes (lane = input,
+//     column = four samples); after the XOR-and-mask decode the registers go
+//     to tensor memory unchanged, one store for the real codes and one for the
+//     imaginary codes;
+//   * the column tile's real and imaginary planes are decoded into shared
+//     memory as before (MN-major, 128-byte swizzle) and are the MMAs' B;
+//   * per 32-sample step the MMAs are Re|-Im += A_re [B_re | B_im],
+//     Re += A_im B_im, -Im += -A_im B_re, A read from tensor memory.
+//
+// Tensor memory holds the accumulator [Re | -Im] in columns 0-255 and DEC A
+// stages (real then imaginary codes, KT / 2 columns) in columns 256-511, so
+// the accumulator is single-buffered.  The epilogue therefore frees it in one
+// quick pass, converting and correcting into a shared-memory tile of the whole
+// tile pair (128 x 128 int32 pairs), and writes that tile to HBM while the
+// MMAs already run the next tile pair; the decoders keep filling the rings in
+// the meantime.
+//
+// The per-input sums S = sum_t u that undo the offset (see xcorr_tc_fused.cu)
+// come from the A path for the rows (dp4a over the codes each thread holds)
+// and from the B path for the columns (byte lanes, as in the other kernel).
+//
+// Warp roles (448 threads, one CTA per SM): warps 0-3 drain the accumulator
+// and write the output;
+// warps 4-11 decode (warp w writes the A lanes of TMEM quarter w % 4, 16
+// inputs, and a share of B); warp 12 is the TMA producer with the L2
+// prefetch; warp 13 owns tensor memory and issues the MMAs.  Every wait is
+// bounded (sm103_ptx.cuh).
+#include "fused_common.cuh"
+#include "sm103_ptx.cuh"
+#include "xcorr_internal.h"
+
+namespace xc {
+namespace {
+
+using namespace fused;
+
+constexpr int kEpiWarps = 4;
+constexpr int kDecWarp0 = 4;
+constexpr int kDecWarps = 8;  // two per tensor-memory lane quarter
+constexpr int kProducerWarp = kDecWarp0 + kDecWarps;
+constexpr int kMmaWarp = kProducerWarp + 1;
+constexpr int kThreads = (kMmaWarp + 1) * 32;
+constexpr int kDecThreads = kDecWarps * 32;
+constexpr int kChunk = 16;
+constexpr int kPitch = kChunk + 1;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kStashCol = 256;                       // 128 columns of corrected Im after the accumulator
+constexpr uint32_t kAcol0 = 384;                          // then the A stages
+constexpr int kStagingBytes = kBlk * kBlk * 4;            // corrected Re of a whole tile pair
+constexpr int kTransposeBytes = kEpiWarps * 32 * kPitch * 8;  // per-warp (Re, Im) transpose for the stores
+constexpr int kSumsBytes = 2 * 2 * kBlk * 8;              // [item parity][rows I, columns J][input] (8P, 8Q)
+// Every partial sum of u_a u_b is n 2^-18 with 0 <= n <= 450 T (and |n| <= 225 T for Im).
+// For T <= kMagicSamples, |n| < 2^22 and n + 1.5 2^23 is exact in FP32, so one FFMA
+// against that constant turns the accumulator into n (in the low bits of the result).
+constexpr int kMagicSamples = 9320;
+constexpr float kMagic = 12582912.0f;       // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+constexpr int kScratchBytes = kDecWarps * 8 * kPitch * 8; // [decoder warp][chunk][input] (P, Q), padded rows
+constexpr int kBarrierBytes = 512;
+
+template <int KT, int RAW, int DEC>
+struct TGeom {
+  static constexpr int kTile = KT * kBlk;      // one 128-input x KT-sample tile of bytes
+  static constexpr int kRawStage = 2 * kTile;  // raw I, raw J
+  static constexpr int kBStage = 2 * kTile;    // B real codes, B imaginary codes
+  static constexpr int kAcols = KT / 2;        // one A stage: KT / 4 columns of real codes, then imaginary
+  static constexpr int kRowsB = KT / (kDecThreads / 8);  // B rows per decoder thread and stage
+  static constexpr int kSteps = KT / 32;                 // MMA steps (32 samples) per stage
+  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kBStage + kStagingBytes + kTransposeBytes + kSumsBytes +
+                               kScratchBytes + kBarrierBytes;
+  static_assert(KT % 32 == 0, "stages hold whole MMA steps and whole 32-row B passes");
+  static_assert(DEC * kAcols <= static_cast<int>(kTmemCols - kAcol0), "A stages fit beside the accumulator");
+  static_assert((2 * RAW + 2 * DEC + 7) * 8 + 8 <= kBarrierBytes, "barrier area");
+  static_assert(kSmem <= 232448, "shared memory budget");
+};
+
+struct TParams {
+  int n_chan, n_inputs, n_tile_pairs;
+  int t0;              // first sample of this launch
+  int n_kt;            // stages per tile pair
+  int64_t n_pairs;
+  int accumulate;      // add into out (else store)
+  int2* out;
+  int* status;
+  uint32_t one;        // 1: a multiplier the compiler cannot fold (see lane_add)
+};
+
+template <int KT, int RAW, int DEC>
+__global__ void __launch_bounds__(kThreads, 1)
+    xcorr_tc_fused_ta_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ TParams p) {
+  using G = TGeom<KT, RAW, DEC>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* raw = smem;
+  uint8_t* bpl = raw + RAW * G::kRawStage;
+  int* staging = reinterpret_cast<int*>(bpl + DEC * G::kBStage);  // Re [row][16-byte chunk ^ (row % 8)]
+  int2* transpose = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(staging) + kStagingBytes);
+  int2* sums = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(transpose) + kTransposeBytes);
+  int2* scratch = sums + 2 * 2 * kBlk;
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(scratch) + kScratchBytes);
+  uint64_t* raw_empty = raw_full + RAW;
+  uint64_t* dec_full = raw_empty + RAW;
+  uint64_t* dec_empty = dec_full + DEC;
+  uint64_t* tfull = dec_empty + DEC;  // the accumulator holds an item
+  uint64_t* tempty = tfull + 1;       // the epilogue has the item in registers
+  uint64_t* sfull = tempty + 1;       // [2] an item's input sums are written
+  uint64_t* sempty = sfull + 2;       // [2] the epilogue is done with them
+  uint64_t* mma_done = sempty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RAW; ++s) {
+      mbar_init(&raw_full[s], 1);
+      mbar_init(&raw_empty[s], kDecWarps);
+    }
+    for (int s = 0; s < DEC; ++s) {
+      mbar_init(&dec_full[s], kDecWarps);
+      mbar_init(&dec_empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, kEpiWarps);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sfull[b], 1);
+      mbar_init(&sempty[b], kEpiWarps);
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == kMmaWarp) tmem_alloc(tslot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int n_items = p.n_chan * p.n_tile_pairs;
+
+  if (warp == kProducerWarp) {
+    if (lane == 0) {
+      constexpr int kAhead = kPrefetchSamples / KT;  // L2 prefetch runs this many stages ahead of the loads
+      prefetch_tmap(&raw_map);
+      {
+        const Item first = item_at(p.n_tile_pairs, blockIdx.x, n_items);
+        for (int s = 0; s < kAhead; ++s) prefetch_stage<KT>(&raw_map, p.t0, p.n_kt, first, s);
+      }
+      int r = 0;
+      uint32_t ph = 0, filled = 0, fill_parity[RAW] = {};
+      bool ok = true;
+      for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
+        const Item it = item_at(p.n_tile_pairs, item, n_items);
+        for (int tb = 0; tb < p.n_kt; ++tb) {
+          if (tb + kAhead < p.n_kt)
+            prefetch_stage<KT>(&raw_map, p.t0, p.n_kt, it, tb + kAhead);
+          else
+            prefetch_stage<KT>(&raw_map, p.t0, p.n_kt, item_at(p.n_tile_pairs, item + gridDim.x, n_items),
+                               tb + kAhead - p.n_kt);
+          if (!mbar_wait(&raw_empty[r], ph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = raw + r * G::kRawStage;
+          const int t = p.t0 + tb * KT;
+          mbar_expect_tx(&raw_full[r], (it.diag ? 1 : 2) * G::kTile);
+          tma_load_3d(st, &raw_map, &raw_full[r], it.I * kBlk, it.c, t);
+          if (!it.diag) tma_load_3d(st + G::kTile, &raw_map, &raw_full[r], it.J * kBlk, it.c, t);
+          fill_parity[r] = ph;
+          filled |= 1u << r;
+          if (++r == RAW) {
+            r = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      // Let every copy this CTA issued land before the CTA can exit.
+      volatile int never = 0;
+      for (int q = 0; q < RAW; ++q)
+        if (filled & (1u << q)) mbar_wait(&raw_full[q], fill_parity[q], &never, p.status, DEV_TIMEOUT_DRAIN);
+    }
+  } else if (warp >= kDecWarp0 && warp < kDecWarp0 + kDecWarps) {
+    const int dw = warp - kDecWarp0, tid = dw * 32 + lane;
+    // A: this warp's 16 inputs are TMEM lanes 16 ib .. 16 ib + 15, inside its lane quarter warp % 4
+    const int ib = 2 * (warp & 3) + (dw >> 2);
+    const uint32_t a_lanes = static_cast<uint32_t>(16 * ib) << 16;
+    const int arow = lane & 15;                  // ldmatrix row (sample) this thread addresses
+    const int apos = (ib ^ (arow & 7)) << 4;     // chunk ib of that row under the 128-byte swizzle
+    // B: a fixed 16-input chunk L of the column tile, rows phase, phase + 32, ...
+    const int L = tid & 7, phase = tid >> 3;
+    const int bpos = (L ^ (phase & 7)) << 4;
+    int r = 0, d = 0, g = 0;
+    uint32_t rph = 0, dph = 0;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
+      const Item cur = item_at(p.n_tile_pairs, item, n_items);
+      // A sums: inputs 16 ib + lane / 4 (0) and + 8 (1), over samples 4 (lane % 4) .. + 3 of every 16
+      uint32_t sar0 = 0u, sai0 = 0u, sar1 = 0u, sai1 = 0u;
+      // B sums in 16-bit lanes: word e / 2, half e % 2 holds input e of chunk L
+      uint32_t s_re[8], s_im[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s_re[q] = s_im[q] = 0u;
+      bool ok = true;
+      for (int tb = 0; tb < p.n_kt; ++tb) {
+        if (!mbar_wait_warp(&raw_full[r], rph, abort_flag, p.status, DEV_TIMEOUT_FULL) ||
+            !mbar_wait_warp(&dec_empty[d], dph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint8_t* raw_a = raw + r * G::kRawStage;
+        const uint8_t* raw_b = raw_a + (cur.diag ? 0 : G::kTile);
+        // A operand: 16 samples x 16 inputs per ldmatrix, decoded in registers, stored to TMEM
+        const uint32_t ta = tmem + a_lanes + kAcol0 + static_cast<uint32_t>(d * G::kAcols);
+#pragma unroll
+        for (int sb = 0; sb < KT / 16; ++sb) {
+          uint32_t x0, x1, re0, im0, re1, im1;
+          ldmatrix_t_b8(smem_u32(raw_a + (16 * sb + arow) * 128 + apos), x0, x1);
+          offset_codes(x0, re0, im0);
+          offset_codes(x1, re1, im1);
+          sar0 = __dp4a(re0, 0x01010101u, sar0);
+          sai0 = __dp4a(im0, 0x01010101u, sai0);
+          sar1 = __dp4a(re1, 0x01010101u, sar1);
+          sai1 = __dp4a(im1, 0x01010101u, sai1);
+          tmem_st_16x128b(ta + 4 * sb, re0, re1);
+          tmem_st_16x128b(ta + KT / 4 + 4 * sb, im0, im1);
+        }
+        // B operand: real and imaginary planes in shared memory at the raw chunk's swizzled offset
+        {
+          constexpr int R = G::kRowsB;
+          const uint8_t* src = raw_b + bpos;
+          uint8_t* re_t = bpl + d * G::kBStage + bpos;
+          uint8_t* im_t = re_t + G::kTile;
+          uint4 v[R];
+#pragma unroll
+          for (int k = 0; k < R; ++k) v[k] = *reinterpret_cast<const uint4*>(src + (phase + 32 * k) * 128);
+          uint32_t a_re[4] = {0u, 0u, 0u, 0u}, a_im[4] = {0u, 0u, 0u, 0u};  // byte lanes: <= 15 R <= 60
+#pragma unroll
+          for (int k = 0; k < R; ++k) {
+            uint4 re, im;
+            offset_codes(v[k].x, re.x, im.x);
+            offset_codes(v[k].y, re.y, im.y);
+            offset_codes(v[k].z, re.z, im.z);
+            offset_codes(v[k].w, re.w, im.w);
+            lane_add(a_re[0], re.x, p.one), lane_add(a_re[1], re.y, p.one);
+            lane_add(a_re[2], re.z, p.one), lane_add(a_re[3], re.w, p.one);
+            lane_add(a_im[0], im.x, p.one), lane_add(a_im[1], im.y, p.one);
+            lane_add(a_im[2], im.z, p.one), lane_add(a_im[3], im.w, p.one);
+            const int off = (phase + 32 * k) * 128;
+            *reinterpret_cast<uint4*>(re_t + off) = re;
+            *reinterpret_cast<uint4*>(im_t + off) = im;
+          }
+          // widen to 16-bit lanes: inputs (4q, 4q+1) -> word 2q, (4q+2, 4q+3) -> word 2q+1
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            lane_add(s_re[2 * q], __byte_perm(a_re[q], 0u, 0x4140), p.one);
+            lane_add(s_re[2 * q + 1], __byte_perm(a_re[q], 0u, 0x4342), p.one);
+            lane_add(s_im[2 * q], __byte_perm(a_im[q], 0u, 0x4140), p.one);
+            lane_add(s_im[2 * q + 1], __byte_perm(a_im[q], 0u, 0x4342), p.one);
+          }
+        }
+        // the MMA reads A through tensor memory and B through the async proxy
+        tmem_st_wait();
+        tc_fence_before();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&raw_empty[r]);
+          mbar_arrive(&dec_full[d]);
+        }
+        if (++r == RAW) {
+          r = 0;
+          rph ^= 1u;
+        }
+        if (++d == DEC) {
+          d = 0;
+          dph ^= 1u;
+        }
+      }
+      // row sums: the four lanes holding one input's samples are lanes 4k .. 4k + 3
+#pragma unroll
+      for (int m = 1; m <= 2; m <<= 1) {
+        sar0 += __shfl_xor_sync(0xFFFFFFFFu, sar0, m);
+        sai0 += __shfl_xor_sync(0xFFFFFFFFu, sai0, m);
+        sar1 += __shfl_xor_sync(0xFFFFFFFFu, sar1, m);
+        sai1 += __shfl_xor_sync(0xFFFFFFFFu, sai1, m);
+      }
+      // column sums of this warp: lanes L, L + 8, L + 16, L + 24 hold chunk L
+      int2 pq[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int sr = static_cast<int>((s_re[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
+        const int si = static_cast<int>((s_im[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
+        pq[e] = make_int2(sr + si, si - sr);
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        pq[e].x += __shfl_xor_sync(0xFFFFFFFFu, pq[e].x, 8);
+        pq[e].y += __shfl_xor_sync(0xFFFFFFFFu, pq[e].y, 8);
+        pq[e].x += __shfl_xor_sync(0xFFFFFFFFu, pq[e].x, 16);
+        pq[e].y += __shfl_xor_sync(0xFFFFFFFFu, pq[e].y, 16);
+      }
+      if (lane < 8) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) scratch[(dw * 8 + lane) * kPitch + e] = pq[e];
+      }
+      dec_bar_sync(kDecThreads);
+      const int buf = g & 1;
+      if (ok) ok = mbar_wait_warp(&sempty[buf], ((g >> 1) & 1) ^ 1, abort_flag, p.status, DEV_TIMEOUT_TMEM_EMPTY);
+      if (ok) {
+        int2* rows = sums + (buf * 2) * kBlk;
+        if ((lane & 3) == 0) {
+          const int e = 16 * ib + (lane >> 2);
+          rows[e] = make_int2(8 * static_cast<int>(sar0 + sai0), 8 * (static_cast<int>(sai0) - static_cast<int>(sar0)));
+          rows[e + 8] =
+              make_int2(8 * static_cast<int>(sar1 + sai1), 8 * (static_cast<int>(sai1) - static_cast<int>(sar1)));
+        }
+        if (tid < kBlk) {
+          const int e = tid;
+          int2 s = make_int2(0, 0);
+#pragma unroll
+          for (int w = 0; w < kDecWarps; ++w) {
+            const int2 x = scratch[(w * 8 + (e >> 4)) * kPitch + (e & 15)];
+            s.x += x.x;
+            s.y += x.y;
+          }
+          sums[(buf * 2 + 1) * kBlk + e] = make_int2(8 * s.x, 8 * s.y);
+        }
+      }
+      if (dec_bar_or(!ok || *abort_flag, kDecThreads)) break;
+      if (tid == 0) mbar_arrive(&sfull[buf]);
+    }
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      const uint32_t id256 = instr_desc_ta(kTypeE4M3, 128, 256, false);
+      const uint32_t id128 = instr_desc_ta(kTypeE4M3, 128, 128, false);
+      const uint32_t id128n = instr_desc_ta(kTypeE4M3, 128, 128, true);
+      constexpr uint32_t kLbo = G::kTile;  // B real and imaginary planes are adjacent 128-byte-wide chunks
+      int d = 0, g = 0;
+      uint32_t dph = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x, ++g) {
+        if (!mbar_wait(tempty, (g & 1) ^ 1, abort_flag, p.status, DEV_TIMEOUT_TMEM_EMPTY)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int tb = 0; tb < p.n_kt; ++tb) {
+          if (!mbar_wait(&dec_full[d], dph, abort_flag, p.status, DEV_TIMEOUT_FULL)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_r = tmem + kAcol0 + static_cast<uint32_t>(d * G::kAcols);
+          const uint32_t a_i = a_r + KT / 4;
+          const uint32_t b_r = smem_u32(bpl + d * G::kBStage);
+          const uint32_t b_i = b_r + G::kTile;
+#pragma unroll
+          for (int k = 0; k < G::kSteps; ++k) {
+            const uint32_t off = static_cast<uint32_t>(k * 32 * 128);  // 32 rows of 128 B
+            const uint32_t first = (tb == 0 && k == 0) ? 1u : 0u;
+            mma_f8f6f4_ta(tmem, a_r + 8 * k, smem_desc_sw128(b_r + off, kLbo, 1024), id256, first ^ 1u);
+            mma_f8f6f4_ta(tmem, a_i + 8 * k, smem_desc_sw128(b_i + off, kLbo, 1024), id128, 1u);
+            mma_f8f6f4_ta(tmem + 128, a_i + 8 * k, smem_desc_sw128(b_r + off, kLbo, 1024), id128n, 1u);
+          }
+          mma_commit(&dec_empty[d]);
+          if (++d == DEC) {
+            d = 0;
+            dph ^= 1u;
+          }
+        }
+        if (ok) mma_commit(tfull);
+      }
+      volatile int never = 0;
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0, &never, p.status, DEV_TIMEOUT_DRAIN);
+    }
+  } else if (warp < kEpiWarps) {
+    // Epilogue, warp w = tile rows 32w .. 32w + 31 (TMEM lanes of quarter w).  Phase 1 frees the
+    // accumulator: corrected Re to the shared-memory staging tile, corrected Im to the TMEM stash.
+    // Phase 2 joins them through the warp's transpose buffer and writes the rows out while the
+    // MMAs run the next tile pair.
+    const int half = lane >> 4, col = lane & 15;
+    const int r_own = warp * 32 + lane;  // this thread's tile row
+    const int t128 = 128 * p.n_kt * KT;  // 128 T over the padded block (padding decodes to u = 8 + 8i)
+    const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    int4* srow = reinterpret_cast<int4*>(staging + r_own * kBlk);  // 16-byte chunks, XOR-swizzled by row
+    const int sw = r_own & 7;
+    int2* tbuf = transpose + warp * 32 * kPitch;
+    int g = 0;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
+      const int c = item / p.n_tile_pairs;
+      int I, J;
+      tile_pair(item - c * p.n_tile_pairs, I, J);
+      int2* out_c = p.out + (int64_t)c * p.n_pairs;
+      const int row0 = I * kBlk + warp * 32;
+      const int buf = g & 1;
+      if (!mbar_wait_warp(tfull, g & 1, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL) ||
+          !mbar_wait_warp(&sfull[buf], (g >> 1) & 1, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL))
+        break;
+      tc_fence_after();
+      // 16-pair chunks this warp keeps: none past the inputs, none wholly above the diagonal
+      const int n_ch = row0 >= p.n_inputs ? 0 : I == J ? (warp * 32 + 31) / kChunk + 1 : kBlk / kChunk;
+      {
+        const int2 rs = sums[(buf * 2) * kBlk + r_own];  // (8P, 8Q) of this row's input
+        const int4* cs4 = reinterpret_cast<const int4*>(sums + (buf * 2 + (I == J ? 0 : 1)) * kBlk);
+        const bool magic = t128 <= 128 * kMagicSamples;
+        // Re = n_re - 8 P_a - 8 P_b + 128 T,  Im = -n_im - 8 Q_a + 8 Q_b
+        const int row_re = t128 - rs.x - (magic ? kMagicBits : 0);
+        const int row_im = -rs.y + (magic ? kMagicBits : 0);
+        for (int ch = 0; ch < n_ch; ++ch) {
+          uint32_t re[16], nim[16];
+          tmem_ld16(taddr + kChunk * ch, re);
+          tmem_ld16(taddr + 128 + kChunk * ch, nim);
+          // the column sums first: the staging stores below would otherwise hold back every load
+          int4 s[kChunk / 2];
+#pragma unroll
+          for (int k = 0; k < kChunk / 2; ++k) s[k] = cs4[(kChunk * ch) / 2 + k];  // (8P, 8Q) of 2k, 2k + 1
+          tmem_ld_wait();
+#pragma unroll
+          for (int q = 0; q < kChunk; ++q) {
+            re[q] = magic ? __float_as_uint(fmaf(__uint_as_float(re[q]), 262144.0f, kMagic))
+                          : static_cast<uint32_t>(__float2int_rn(__uint_as_float(re[q]) * 262144.0f));
+            nim[q] = magic ? __float_as_uint(fmaf(__uint_as_float(nim[q]), 262144.0f, kMagic))
+                           : static_cast<uint32_t>(__float2int_rn(__uint_as_float(nim[q]) * 262144.0f));
+          }
+#pragma unroll
+          for (int k = 0; k < kChunk / 2; ++k) {
+            re[2 * k] = static_cast<uint32_t>(static_cast<int>(re[2 * k]) + row_re - s[k].x);
+            re[2 * k + 1] = static_cast<uint32_t>(static_cast<int>(re[2 * k + 1]) + row_re - s[k].z);
+            nim[2 * k] = static_cast<uint32_t>(-static_cast<int>(nim[2 * k]) + row_im + s[k].y);
+            nim[2 * k + 1] = static_cast<uint32_t>(-static_cast<int>(nim[2 * k + 1]) + row_im + s[k].w);
+          }
+          tmem_st16(taddr + kStashCol + kChunk * ch, nim);
+#pragma unroll
+          for (int k = 0; k < kChunk / 4; ++k)
+            srow[((kChunk * ch) / 4 + k) ^ sw] = make_int4(static_cast<int>(re[4 * k]), static_cast<int>(re[4 * k + 1]),
+                                                           static_cast<int>(re[4 * k + 2]),
+                                                           static_cast<int>(re[4 * k + 3]));
+        }
+      }
+      // the accumulator and the input sums are free once the stash stores have landed
+      tmem_st_wait();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(tempty);
+        mbar_arrive(&sempty[buf]);
+      }
+      // phase 2: per 16-column chunk, this thread's row (Re, Im) into the transpose buffer, then a
+      // half-warp writes 16 consecutive pairs of one row
+      for (int ch = 0; ch < n_ch; ++ch) {
+        uint32_t im[16];
+        tmem_ld16(taddr + kStashCol + kChunk * ch, im);
+        int4 re4[kChunk / 4];
+#pragma unroll
+        for (int k = 0; k < kChunk / 4; ++k) re4[k] = srow[((kChunk * ch) / 4 + k) ^ sw];
+        tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < kChunk / 4; ++k) {
+          tbuf[lane * kPitch + 4 * k] = make_int2(re4[k].x, static_cast<int>(im[4 * k]));
+          tbuf[lane * kPitch + 4 * k + 1] = make_int2(re4[k].y, static_cast<int>(im[4 * k + 1]));
+          tbuf[lane * kPitch + 4 * k + 2] = make_int2(re4[k].z, static_cast<int>(im[4 * k + 2]));
+          tbuf[lane * kPitch + 4 * k + 3] = make_int2(re4[k].w, static_cast<int>(im[4 * k + 3]));
+        }
+        __syncwarp();
+        const int j = J * kBlk + kChunk * ch + col;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int2 v[8];  // the staged values first, then the stores
+#pragma unroll
+          for (int r = 0; r < 8; ++r) v[r] = tbuf[(2 * (8 * h + r) + half) * kPitch + col];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int i = row0 + 2 * (8 * h + r) + half;
+            if (i < p.n_inputs && j <= i) {
+              int2* dst = out_c + (int64_t)i * (i + 1) / 2 + j;
+              if (p.accumulate) {
+                const int2 o = *dst;
+                v[r].x += o.x;
+                v[r].y += o.y;
+              }
+              *dst = v[r];
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+template <int KT, int RAW, int DEC>
+cudaError_t launch_ta(const CUtensorMap& raw_map, const TParams& p, int grid, cudaStream_t stream) {
+  using G = TGeom<KT, RAW, DEC>;
+  auto kern = xcorr_tc_fused_ta_kernel<KT, RAW, DEC>;
+  static int attr_device = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (attr_device != dev) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_device = dev;
+  }
+  kern<<<grid, kThreads, G::kSmem, stream>>>(raw_map, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// The tensor-memory-A shapes: 64 samples with 4 raw + 4 decoded stages, 128 samples with 2 + 2,
+// 64 samples with 5 + 3.
+int fused_ta_stage_samples(int variant) { return variant == 1 ? 128 : 64; }
+
+cudaError_t launch_xcorr_tc_fused_ta_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
+                                         int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
+                                         cudaStream_t stream) {
+  const int nb = (n_inputs + kBlk - 1) / kBlk;
+  const int kt = fused_ta_stage_samples(variant);
+  if (n_time <= 0 || n_inputs % 16 != 0 || reinterpret_cast<uintptr_t>(in) % 16 != 0 ||
+      kFusedWindowCI4 % kt != 0)
+    return cudaErrorInvalidValue;
+  TParams p{};
+  p.n_chan = n_chan;
+  p.n_inputs = n_inputs;
+  p.n_tile_pairs = nb * (nb + 1) / 2;
+  p.n_pairs = (int64_t)n_inputs * (n_inputs + 1) / 2;
+  p.out = out;
+  p.status = status;
+  p.one = 1u;
+  const int64_t items = (int64_t)n_chan * p.n_tile_pairs;
+  const int grid = static_cast<int>(items < num_sms ? items : num_sms);
+  CUtensorMap raw_map;
+  if (row_chans < n_chan || !encode_raw_ci4_tmap(&raw_map, in, n_inputs, n_chan, row_chans, n_time, kt, nullptr))
+    return cudaErrorInvalidValue;
+  // one exactly-summed block per launch; later blocks add into the first
+  for (int t0 = 0; t0 < n_time; t0 += kFusedWindowCI4) {
+    const int len = n_time - t0 < kFusedWindowCI4 ? n_time - t0 : kFusedWindowCI4;
+    p.t0 = t0;
+    p.n_kt = (len + kt - 1) / kt;
+    p.accumulate = (accumulate || t0 > 0) ? 1 : 0;
+    cudaError_t e;
+    switch (variant) {
+      case 0: e = launch_ta<64, 4, 4>(raw_map, p, grid, stream); break;
+      case 1: e = launch_ta<128, 2, 2>(raw_map, p, grid, stream); break;
+      default: e = launch_ta<64, 5, 3>(raw_map, p, grid, stream); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace xc
