@@ -63,9 +63,11 @@ WORKLOADS = {
 WORKLOAD = WORKLOADS["ci4_512in"]
 # ncu DRAM traffic of the headline kernel per launch, stored beside the source hash it was taken on
 KERNEL_SOURCES = {
-    "xcorr_tc_fused_kernel": ("xcorr_tc_fused.cu", "sm103_ptx.cuh", "xcorr_internal.h"),
+    "xcorr_tc_fused_ta_kernel": ("xcorr_tc_fused_ta.cu", "fused_common.cuh", "sm103_ptx.cuh", "xcorr_internal.h"),
+    "xcorr_tc_fused_kernel": ("xcorr_tc_fused.cu", "fused_common.cuh", "sm103_ptx.cuh", "xcorr_internal.h"),
     "xcorr_tc_kernel": ("xcorr_tc.cu", "sm103_ptx.cuh", "xcorr_internal.h"),
 }
+FUSED_TA_VARIANTS = (4, 5, 6)  # tuning stage_variants served by the tensor-memory-A fused kernel
 
 
 def profile_summary_path(kernel: str) -> str:
@@ -402,7 +404,8 @@ def our_arm(args) -> int:
         tuning, _ = (plan.query()["tuning"], None) if args.no_autotune else plan.autotune(xd)
     launches_per_step = plan.query()["kernels_per_execute"]  # all launches of one execute
     fused = fmt == "ci4" and tuning["unfused"] == 0
-    x_kernel = "xcorr_tc_fused_kernel" if fused else "xcorr_tc_kernel"
+    fused_ta = fused and tuning["stage_variant"] in FUSED_TA_VARIANTS
+    x_kernel = ("xcorr_tc_fused_ta_kernel" if fused_ta else "xcorr_tc_fused_kernel") if fused else "xcorr_tc_kernel"
     x_launches = launches_per_step if fused else launches_per_step // 2  # else unpack + X per channel group
     out_dtype = torch.float32 if fmt == "cf32" else torch.int32
     out = torch.empty((n_chan, n_pairs, 2), dtype=out_dtype, device=dev)
@@ -508,7 +511,11 @@ def our_arm(args) -> int:
                              "uniform": "4+4-bit complex, uniform integers in [-7, 7]",
                              "gauss8": "int8 complex, Gaussian sigma 20 clipped to +-127",
                              "gauss32": "float32 complex, Gaussian sigma 1"}[w["gen"]],
-                   "engine": {"ci4": ("tcgen05 kind::f8f6f4, unpack fused on chip (offset-binary "
+                   "engine": {"ci4": ("tcgen05 kind::f8f6f4, unpack fused on chip, A operand decoded "
+                                      "into tensor memory (ldmatrix.trans + tcgen05.st), B in shared "
+                                      "memory (offset-binary E4M3 codes u = t + 8, exact FP32 TMEM "
+                                      "sums, per-input sum correction, int32 out)") if fused_ta else
+                                     ("tcgen05 kind::f8f6f4, unpack fused on chip (offset-binary "
                                       "E4M3 codes u = t + 8, exact FP32 TMEM sums, per-input sum "
                                       "correction, int32 out)") if fused else
                                      ("tcgen05 kind::f8f6f4 (E4M3 codes of 4-bit integers, exact "

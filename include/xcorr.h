@@ -100,7 +100,8 @@ typedef struct {
                            samples with 8 decoder warps, or 96 x (4 + 2) with 12 (both
                            operands decoded into shared memory); 4 .. 6: the A operand
                            decoded into tensor memory, raw / decoded rings of
-                           64 x (2 + 3), 32 x (4 + 6), 64 x (3 + 2) samples;
+                           128 x (2 + 2), 96 x (3 + 2), 64 x (4 + 4) samples (4 is the
+                           default of a 4-bit plan);
                            1 = always through E4M3 planes in HBM                            */
 } xcorr_tuning;
 

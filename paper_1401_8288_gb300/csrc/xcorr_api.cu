@@ -335,6 +335,9 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
   plan->planes_per_chan = ppc;
   plan->window_samples = c.fmt == XCORR_IN_CI4 ? xc::kTcWindowCI4 : xc::kTcWindowBF16;
   plan->exp_windows = exp_windows;
+  // 4-bit input starts on the fused kernel with the A operand in tensor memory (the fastest
+  // shape measured); the planes path reads the same tuning as its 4 x 48 KB ring
+  plan->tune_variant = c.fmt == XCORR_IN_CI4 ? xc::kDefaultFusedVariant : 0;
 
   if ((e = cudaMalloc(&plan->acc, acc_bytes)) != cudaSuccess ||
       (planes_bytes && (e = cudaMalloc(&plan->planes, planes_bytes)) != cudaSuccess) ||

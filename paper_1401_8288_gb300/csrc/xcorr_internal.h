@@ -32,6 +32,7 @@ constexpr int kTcWindowBF16 = 384;
 constexpr int kFusedWindowCI4 = 37248;
 constexpr int kTcVariants = 3;     // planes-path stage shapes: 64 KB x 3, 48 KB x 4, 32 KB x 6
 constexpr int kFusedVariants = 7;  // fused 4-bit kernel shapes (the tuning's stage_variant range)
+constexpr int kDefaultFusedVariant = 4;  // 4-bit plans before any tuning: A in tensor memory, 128 x (2 + 2)
 // The planes path's shape for a tuning's stage_variant (3 exists only for the fused kernel).
 inline int planes_variant(int v) { return v >= kTcVariants ? 1 : v; }
 constexpr int64_t kMaxIntegrationCF32 = INT64_C(16777216);  // FP32 per dump, widen beyond

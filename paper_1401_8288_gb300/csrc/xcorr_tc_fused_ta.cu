@@ -59,8 +59,9 @@ constexpr int kPitch = kChunk + 1;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kStashCol = 256;                       // 128 columns of corrected Im after the accumulator
 constexpr uint32_t kAcol0 = 384;                          // then the A stages
-constexpr int kStagingBytes = kBlk * kBlk * 4;            // corrected Re of a whole tile pair
-constexpr int kTransposeBytes = kEpiWarps * 32 * kPitch * 8;  // per-warp (Re, Im) transpose for the stores
+constexpr int kStagingBytes = kBlk * kBlk * 4;            // Re accumulator bits of a whole tile pair
+constexpr int kTransposeBytes = kEpiWarps * 32 * kPitch * 4;  // per-warp Im transpose for the stores
+constexpr int kRowcBytes = kBlk * 8;                      // per-row correction constants
 constexpr int kSumsBytes = 2 * 2 * kBlk * 8;              // [item parity][rows I, columns J][input] (8P, 8Q)
 // Every partial sum of u_a u_b is n 2^-18 with 0 <= n <= 450 T (and |n| <= 225 T for Im).
 // For T <= kMagicSamples, |n| < 2^22 and n + 1.5 2^23 is exact in FP32, so one FFMA
@@ -79,8 +80,8 @@ struct TGeom {
   static constexpr int kAcols = KT / 2;        // one A stage: KT / 4 columns of real codes, then imaginary
   static constexpr int kRowsB = KT / (kDecThreads / 8);  // B rows per decoder thread and stage
   static constexpr int kSteps = KT / 32;                 // MMA steps (32 samples) per stage
-  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kBStage + kStagingBytes + kTransposeBytes + kSumsBytes +
-                               kScratchBytes + kBarrierBytes;
+  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kBStage + kStagingBytes + kTransposeBytes + kRowcBytes +
+                               kSumsBytes + kScratchBytes + kBarrierBytes;
   static_assert(KT % 32 == 0, "stages hold whole MMA steps and whole 32-row B passes");
   static_assert(DEC * kAcols <= static_cast<int>(kTmemCols - kAcol0), "A stages fit beside the accumulator");
   static_assert((2 * RAW + 2 * DEC + 7) * 8 + 8 <= kBarrierBytes, "barrier area");
@@ -98,6 +99,11 @@ struct TParams {
   uint32_t one;        // 1: a multiplier the compiler cannot fold (see lane_add)
 };
 
+// 16-byte chunk swizzle of the Re staging tile: a bijection of row % 8, so the eight rows of a
+// phase-1 quarter-warp store hit eight distinct chunks, and rows 2k, 2k + 1 (the two half-warps
+// of a phase-2 load) land in opposite halves of each eight-chunk group.
+__device__ __forceinline__ int staging_swizzle(int row) { return ((row & 1) << 2) | ((row >> 1) & 3); }
+
 template <int KT, int RAW, int DEC>
 __global__ void __launch_bounds__(kThreads, 1)
     xcorr_tc_fused_ta_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ TParams p) {
@@ -106,9 +112,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* raw = smem;
   uint8_t* bpl = raw + RAW * G::kRawStage;
-  int* staging = reinterpret_cast<int*>(bpl + DEC * G::kBStage);  // Re [row][16-byte chunk ^ (row % 8)]
-  int2* transpose = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(staging) + kStagingBytes);
-  int2* sums = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(transpose) + kTransposeBytes);
+  uint32_t* staging = reinterpret_cast<uint32_t*>(bpl + DEC * G::kBStage);  // Re [row][16-byte chunk ^ swz(row)]
+  uint32_t* transpose = staging + kBlk * kBlk;                              // [warp][32][kPitch]
+  int2* rowc = reinterpret_cast<int2*>(transpose + kEpiWarps * 32 * kPitch);  // [row]
+  int2* sums = rowc + kBlk;
   int2* scratch = sums + 2 * 2 * kBlk;
   uint64_t* raw_full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(scratch) + kScratchBytes);
   uint64_t* raw_empty = raw_full + RAW;
@@ -386,17 +393,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(mma_done, 0, &never, p.status, DEV_TIMEOUT_DRAIN);
     }
   } else if (warp < kEpiWarps) {
-    // Epilogue, warp w = tile rows 32w .. 32w + 31 (TMEM lanes of quarter w).  Phase 1 frees the
-    // accumulator: corrected Re to the shared-memory staging tile, corrected Im to the TMEM stash.
-    // Phase 2 joins them through the warp's transpose buffer and writes the rows out while the
-    // MMAs run the next tile pair.
+    // Epilogue, warp w = tile rows 32w .. 32w + 31 (TMEM lanes of quarter w).  Phase 1 only moves
+    // the accumulator out, so that it is free as soon as possible: Re bits to the shared-memory
+    // staging tile, Im bits to the TMEM stash.  Phase 2, while the MMAs run the next tile pair,
+    // converts, applies the offset corrections and writes the rows; Im goes through the warp's
+    // transpose buffer so that a half-warp writes 16 consecutive pairs of one row.
     const int half = lane >> 4, col = lane & 15;
-    const int r_own = warp * 32 + lane;  // this thread's tile row
+    const int r_own = warp * 32 + lane;  // this thread's tile row in phase 1
     const int t128 = 128 * p.n_kt * KT;  // 128 T over the padded block (padding decodes to u = 8 + 8i)
+    const bool magic = t128 <= 128 * kMagicSamples;
     const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    int4* srow = reinterpret_cast<int4*>(staging + r_own * kBlk);  // 16-byte chunks, XOR-swizzled by row
-    const int sw = r_own & 7;
-    int2* tbuf = transpose + warp * 32 * kPitch;
+    uint32_t* tim = transpose + warp * 32 * kPitch;
     int g = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
       const int c = item / p.n_tile_pairs;
@@ -412,90 +419,78 @@ __global__ void __launch_bounds__(kThreads, 1)
       // 16-pair chunks this warp keeps: none past the inputs, none wholly above the diagonal
       const int n_ch = row0 >= p.n_inputs ? 0 : I == J ? (warp * 32 + 31) / kChunk + 1 : kBlk / kChunk;
       {
-        const int2 rs = sums[(buf * 2) * kBlk + r_own];  // (8P, 8Q) of this row's input
-        const int4* cs4 = reinterpret_cast<const int4*>(sums + (buf * 2 + (I == J ? 0 : 1)) * kBlk);
-        const bool magic = t128 <= 128 * kMagicSamples;
-        // Re = n_re - 8 P_a - 8 P_b + 128 T,  Im = -n_im - 8 Q_a + 8 Q_b
-        const int row_re = t128 - rs.x - (magic ? kMagicBits : 0);
-        const int row_im = -rs.y + (magic ? kMagicBits : 0);
+        uint4* srow = reinterpret_cast<uint4*>(staging + r_own * kBlk);
+        const int sw = staging_swizzle(r_own);
         for (int ch = 0; ch < n_ch; ++ch) {
           uint32_t re[16], nim[16];
           tmem_ld16(taddr + kChunk * ch, re);
           tmem_ld16(taddr + 128 + kChunk * ch, nim);
-          // the column sums first: the staging stores below would otherwise hold back every load
-          int4 s[kChunk / 2];
-#pragma unroll
-          for (int k = 0; k < kChunk / 2; ++k) s[k] = cs4[(kChunk * ch) / 2 + k];  // (8P, 8Q) of 2k, 2k + 1
           tmem_ld_wait();
-#pragma unroll
-          for (int q = 0; q < kChunk; ++q) {
-            re[q] = magic ? __float_as_uint(fmaf(__uint_as_float(re[q]), 262144.0f, kMagic))
-                          : static_cast<uint32_t>(__float2int_rn(__uint_as_float(re[q]) * 262144.0f));
-            nim[q] = magic ? __float_as_uint(fmaf(__uint_as_float(nim[q]), 262144.0f, kMagic))
-                           : static_cast<uint32_t>(__float2int_rn(__uint_as_float(nim[q]) * 262144.0f));
-          }
-#pragma unroll
-          for (int k = 0; k < kChunk / 2; ++k) {
-            re[2 * k] = static_cast<uint32_t>(static_cast<int>(re[2 * k]) + row_re - s[k].x);
-            re[2 * k + 1] = static_cast<uint32_t>(static_cast<int>(re[2 * k + 1]) + row_re - s[k].z);
-            nim[2 * k] = static_cast<uint32_t>(-static_cast<int>(nim[2 * k]) + row_im + s[k].y);
-            nim[2 * k + 1] = static_cast<uint32_t>(-static_cast<int>(nim[2 * k + 1]) + row_im + s[k].w);
-          }
           tmem_st16(taddr + kStashCol + kChunk * ch, nim);
 #pragma unroll
           for (int k = 0; k < kChunk / 4; ++k)
-            srow[((kChunk * ch) / 4 + k) ^ sw] = make_int4(static_cast<int>(re[4 * k]), static_cast<int>(re[4 * k + 1]),
-                                                           static_cast<int>(re[4 * k + 2]),
-                                                           static_cast<int>(re[4 * k + 3]));
+            srow[((kChunk * ch) / 4 + k) ^ sw] = make_uint4(re[4 * k], re[4 * k + 1], re[4 * k + 2], re[4 * k + 3]);
         }
+        // Re = n_re - 8 P_a - 8 P_b + 128 T,  Im = -n_im - 8 Q_a + 8 Q_b: the row's part
+        const int2 rs = sums[(buf * 2) * kBlk + r_own];  // (8P, 8Q) of this row's input
+        rowc[r_own] = make_int2(t128 - rs.x - (magic ? kMagicBits : 0), -rs.y + (magic ? kMagicBits : 0));
       }
-      // the accumulator and the input sums are free once the stash stores have landed
+      // the accumulator is free once the stash stores have landed
       tmem_st_wait();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(tempty);
-        mbar_arrive(&sempty[buf]);
-      }
-      // phase 2: per 16-column chunk, this thread's row (Re, Im) into the transpose buffer, then a
-      // half-warp writes 16 consecutive pairs of one row
+      if (lane == 0) mbar_arrive(tempty);
+      // phase 2
+      const int2* cs = sums + (buf * 2 + (I == J ? 0 : 1)) * kBlk;  // (8P, 8Q) of the columns
       for (int ch = 0; ch < n_ch; ++ch) {
         uint32_t im[16];
         tmem_ld16(taddr + kStashCol + kChunk * ch, im);
-        int4 re4[kChunk / 4];
-#pragma unroll
-        for (int k = 0; k < kChunk / 4; ++k) re4[k] = srow[((kChunk * ch) / 4 + k) ^ sw];
+        const int jl = kChunk * ch + col;  // this lane's column in the tile
+        const int2 s = cs[jl];
         tmem_ld_wait();
 #pragma unroll
-        for (int k = 0; k < kChunk / 4; ++k) {
-          tbuf[lane * kPitch + 4 * k] = make_int2(re4[k].x, static_cast<int>(im[4 * k]));
-          tbuf[lane * kPitch + 4 * k + 1] = make_int2(re4[k].y, static_cast<int>(im[4 * k + 1]));
-          tbuf[lane * kPitch + 4 * k + 2] = make_int2(re4[k].z, static_cast<int>(im[4 * k + 2]));
-          tbuf[lane * kPitch + 4 * k + 3] = make_int2(re4[k].w, static_cast<int>(im[4 * k + 3]));
-        }
+        for (int q = 0; q < kChunk; ++q) tim[lane * kPitch + q] = im[q];
         __syncwarp();
-        const int j = J * kBlk + kChunk * ch + col;
+        const int j = J * kBlk + jl;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          int2 v[8];  // the staged values first, then the stores
+          uint32_t vr[8], vi[8];  // the staged values first, then the stores
+          int2 rc[8];
 #pragma unroll
-          for (int r = 0; r < 8; ++r) v[r] = tbuf[(2 * (8 * h + r) + half) * kPitch + col];
+          for (int r = 0; r < 8; ++r) {
+            const int rl = 2 * (8 * h + r) + half, rr = warp * 32 + rl;
+            vr[r] = staging[rr * kBlk + (((jl >> 2) ^ staging_swizzle(rr)) << 2) + (jl & 3)];
+            vi[r] = tim[rl * kPitch + col];
+            rc[r] = rowc[rr];
+          }
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int i = row0 + 2 * (8 * h + r) + half;
             if (i < p.n_inputs && j <= i) {
+              int nr, ni;
+              if (magic) {
+                nr = __float_as_int(fmaf(__uint_as_float(vr[r]), 262144.0f, kMagic));
+                ni = __float_as_int(fmaf(__uint_as_float(vi[r]), 262144.0f, kMagic));
+              } else {
+                nr = __float2int_rn(__uint_as_float(vr[r]) * 262144.0f);
+                ni = __float2int_rn(__uint_as_float(vi[r]) * 262144.0f);
+              }
+              int2 v = make_int2(nr + rc[r].x - s.x, -ni + rc[r].y + s.y);
               int2* dst = out_c + (int64_t)i * (i + 1) / 2 + j;
               if (p.accumulate) {
                 const int2 o = *dst;
-                v[r].x += o.x;
-                v[r].y += o.y;
+                v.x += o.x;
+                v.y += o.y;
               }
-              *dst = v[r];
+              *dst = v;
             }
           }
         }
         __syncwarp();
       }
+      // the input sums are free
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sempty[buf]);
     }
   }
 
@@ -526,9 +521,8 @@ cudaError_t launch_ta(const CUtensorMap& raw_map, const TParams& p, int grid, cu
 
 }  // namespace
 
-// The tensor-memory-A shapes: 64 samples with 4 raw + 4 decoded stages, 128 samples with 2 + 2,
-// 64 samples with 5 + 3.
-int fused_ta_stage_samples(int variant) { return variant == 1 ? 128 : 64; }
+// The tensor-memory-A shapes: 128 samples with 2 raw + 2 decoded stages, 96 with 3 + 2, 64 with 4 + 4.
+int fused_ta_stage_samples(int variant) { return variant == 0 ? 128 : variant == 1 ? 96 : 64; }
 
 cudaError_t launch_xcorr_tc_fused_ta_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                          int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
@@ -559,9 +553,9 @@ cudaError_t launch_xcorr_tc_fused_ta_ci4(const uint8_t* in, int row_chans, int v
     p.accumulate = (accumulate || t0 > 0) ? 1 : 0;
     cudaError_t e;
     switch (variant) {
-      case 0: e = launch_ta<64, 4, 4>(raw_map, p, grid, stream); break;
-      case 1: e = launch_ta<128, 2, 2>(raw_map, p, grid, stream); break;
-      default: e = launch_ta<64, 5, 3>(raw_map, p, grid, stream); break;
+      case 0: e = launch_ta<128, 2, 2>(raw_map, p, grid, stream); break;
+      case 1: e = launch_ta<96, 3, 2>(raw_map, p, grid, stream); break;
+      default: e = launch_ta<64, 4, 4>(raw_map, p, grid, stream); break;
     }
     if (e != cudaSuccess) return e;
   }
