@@ -45,8 +45,11 @@ __device__ __forceinline__ int64_t packet_base(const DevGeometry& g, int64_t pid
 
 // One warp per packet: its N_t x N_ch runs of N_a bytes go to rows (t, c) of
 // the ring block at input offset f N_a (16-byte vectors), then the packet's
-// arrival bit is set.
-__global__ void __launch_bounds__(256) scatter_packets_kernel(const uint8_t* __restrict__ landing,
+// arrival bit is set.  At most 32 registers a thread (8 blocks of 256 per SM):
+// a block then fits beside the persistent X kernel of the previous block,
+// which leaves 8192 registers of an SM free, so placement keeps up while the
+// X-stage runs.
+__global__ void __launch_bounds__(256, 8) scatter_packets_kernel(const uint8_t* __restrict__ landing,
                                                               const int64_t* __restrict__ codes, int64_t p0,
                                                               int64_t p1, uint8_t* __restrict__ ring,
                                                               uint32_t* __restrict__ bits, DevGeometry g) {
@@ -74,8 +77,8 @@ __global__ void __launch_bounds__(256) scatter_packets_kernel(const uint8_t* __r
 
 // Closing a block: every packet whose bit is clear is zero-filled (a CI4 zero
 // is 0 + 0i), and the slot's bits are cleared for its next block.  One warp
-// per 32 packets (one bitmap word).
-__global__ void __launch_bounds__(256) close_block_kernel(uint8_t* __restrict__ ring, uint32_t* __restrict__ bits,
+// per 32 packets (one bitmap word); at most 32 registers, as for the scatter.
+__global__ void __launch_bounds__(256, 8) close_block_kernel(uint8_t* __restrict__ ring, uint32_t* __restrict__ bits,
                                                           int slot, DevGeometry g) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;

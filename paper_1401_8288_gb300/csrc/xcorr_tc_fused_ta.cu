@@ -412,6 +412,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       int2* out_c = p.out + (int64_t)c * p.n_pairs;
       const int row0 = I * kBlk + warp * 32;
       const int buf = g & 1;
+      if (p.accumulate) {
+        // the sums this tile pair adds to, pulled into L2 while its MMAs run: each thread
+        // prefetches the 128-byte lines of its own row's segment (pairs J*128 .. min(J*128 + 127, i))
+        const int i = I * kBlk + r_own;
+        if (i < p.n_inputs) {
+          const char* a = reinterpret_cast<const char*>(out_c + (int64_t)i * (i + 1) / 2 + J * kBlk);
+          const char* e = a + 8 * ((I == J ? r_own : kBlk - 1) + 1);
+          for (const char* l = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(a) & ~uintptr_t(127)); l < e;
+               l += 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(l < a ? a : l));
+        }
+      }
       if (!mbar_wait_warp(tfull, g & 1, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL) ||
           !mbar_wait_warp(&sfull[buf], (g >> 1) & 1, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL))
         break;
