@@ -60,7 +60,8 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kStashCol = 256;                       // 128 columns of corrected Im after the accumulator
 constexpr uint32_t kAcol0 = 384;                          // then the A stages
 constexpr int kStagingBytes = kBlk * kBlk * 4;            // Re accumulator bits of a whole tile pair
-constexpr int kTransposeBytes = kEpiWarps * 32 * kPitch * 4;  // per-warp Im transpose for the stores
+constexpr int kTPitch = 20;                               // Im transpose rows: 16 words + 16 bytes of pad
+constexpr int kTransposeBytes = kEpiWarps * 32 * kTPitch * 4;  // per-warp Im transpose for the stores
 constexpr int kRowcBytes = kBlk * 8;                      // per-row correction constants
 constexpr int kSumsBytes = 2 * 2 * kBlk * 8;              // [item parity][rows I, columns J][input] (8P, 8Q)
 // Every partial sum of u_a u_b is n 2^-18 with 0 <= n <= 450 T (and |n| <= 225 T for Im).
@@ -113,8 +114,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* raw = smem;
   uint8_t* bpl = raw + RAW * G::kRawStage;
   uint32_t* staging = reinterpret_cast<uint32_t*>(bpl + DEC * G::kBStage);  // Re [row][16-byte chunk ^ swz(row)]
-  uint32_t* transpose = staging + kBlk * kBlk;                              // [warp][32][kPitch]
-  int2* rowc = reinterpret_cast<int2*>(transpose + kEpiWarps * 32 * kPitch);  // [row]
+  uint32_t* transpose = staging + kBlk * kBlk;                               // [warp][32][kTPitch]
+  int2* rowc = reinterpret_cast<int2*>(transpose + kEpiWarps * 32 * kTPitch);  // [row]
   int2* sums = rowc + kBlk;
   int2* scratch = sums + 2 * 2 * kBlk;
   uint64_t* raw_full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(scratch) + kScratchBytes);
@@ -397,13 +398,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     // the accumulator out, so that it is free as soon as possible: Re bits to the shared-memory
     // staging tile, Im bits to the TMEM stash.  Phase 2, while the MMAs run the next tile pair,
     // converts, applies the offset corrections and writes the rows; Im goes through the warp's
-    // transpose buffer so that a half-warp writes 16 consecutive pairs of one row.
-    const int half = lane >> 4, col = lane & 15;
+    // transpose buffer so that four threads write 16 consecutive pairs of one row.
     const int r_own = warp * 32 + lane;  // this thread's tile row in phase 1
     const int t128 = 128 * p.n_kt * KT;  // 128 T over the padded block (padding decodes to u = 8 + 8i)
     const bool magic = t128 <= 128 * kMagicSamples;
     const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    uint32_t* tim = transpose + warp * 32 * kPitch;
+    uint32_t* tim = transpose + warp * 32 * kTPitch;
     int g = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
       const int c = item / p.n_tile_pairs;
@@ -447,54 +447,75 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int2 rs = sums[(buf * 2) * kBlk + r_own];  // (8P, 8Q) of this row's input
         rowc[r_own] = make_int2(t128 - rs.x - (magic ? kMagicBits : 0), -rs.y + (magic ? kMagicBits : 0));
       }
-      // the accumulator is free once the stash stores have landed
-      tmem_st_wait();
+      // the accumulator (columns 0-255) is free once its loads have landed; the stash stores
+      // (columns 256-383) need only land before phase 2 reads them
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty);
-      // phase 2
+      tmem_st_wait();
+      // phase 2: four threads per row, four consecutive columns each (16-byte loads of Re, Im and
+      // the column sums; 16-byte stores where the row's pairs are 16-byte aligned)
       const int2* cs = sums + (buf * 2 + (I == J ? 0 : 1)) * kBlk;  // (8P, 8Q) of the columns
+      const int q4 = lane & 3, rg = lane >> 2;
       for (int ch = 0; ch < n_ch; ++ch) {
         uint32_t im[16];
         tmem_ld16(taddr + kStashCol + kChunk * ch, im);
-        const int jl = kChunk * ch + col;  // this lane's column in the tile
-        const int2 s = cs[jl];
+        const int jl0 = kChunk * ch + 4 * q4;  // this thread's first column in the tile
+        const int4 s01 = *reinterpret_cast<const int4*>(cs + jl0);  // (8P, 8Q) of columns jl0, jl0 + 1
+        const int4 s23 = *reinterpret_cast<const int4*>(cs + jl0 + 2);
         tmem_ld_wait();
+        uint4* trow = reinterpret_cast<uint4*>(tim + lane * kTPitch);
 #pragma unroll
-        for (int q = 0; q < kChunk; ++q) tim[lane * kPitch + q] = im[q];
+        for (int k = 0; k < kChunk / 4; ++k) trow[k] = make_uint4(im[4 * k], im[4 * k + 1], im[4 * k + 2], im[4 * k + 3]);
         __syncwarp();
-        const int j = J * kBlk + jl;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          uint32_t vr[8], vi[8];  // the staged values first, then the stores
-          int2 rc[8];
+        for (int it = 0; it < 4; ++it) {
+          const int rl = 8 * it + rg, rr = warp * 32 + rl, i = I * kBlk + rr;
+          const int last = I == J ? rr : kBlk - 1;  // last column of the row in the tile
+          if (i >= p.n_inputs || jl0 > last) continue;
+          const uint4 re4 =
+              *reinterpret_cast<const uint4*>(staging + rr * kBlk + (((jl0 >> 2) ^ staging_swizzle(rr)) << 2));
+          const uint4 im4 = *reinterpret_cast<const uint4*>(tim + rl * kTPitch + 4 * q4);
+          const int2 rc = rowc[rr];
+          const uint32_t vr[4] = {re4.x, re4.y, re4.z, re4.w}, vi[4] = {im4.x, im4.y, im4.z, im4.w};
+          const int sp[4] = {s01.x, s01.z, s23.x, s23.z}, sq[4] = {s01.y, s01.w, s23.y, s23.w};
+          int2 v[4];
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int rl = 2 * (8 * h + r) + half, rr = warp * 32 + rl;
-            vr[r] = staging[rr * kBlk + (((jl >> 2) ^ staging_swizzle(rr)) << 2) + (jl & 3)];
-            vi[r] = tim[rl * kPitch + col];
-            rc[r] = rowc[rr];
+          for (int k = 0; k < 4; ++k) {
+            int nr, ni;
+            if (magic) {
+              nr = __float_as_int(fmaf(__uint_as_float(vr[k]), 262144.0f, kMagic));
+              ni = __float_as_int(fmaf(__uint_as_float(vi[k]), 262144.0f, kMagic));
+            } else {
+              nr = __float2int_rn(__uint_as_float(vr[k]) * 262144.0f);
+              ni = __float2int_rn(__uint_as_float(vi[k]) * 262144.0f);
+            }
+            v[k] = make_int2(nr + rc.x - sp[k], -ni + rc.y + sq[k]);
           }
+          int2* dst = out_c + (int64_t)i * (i + 1) / 2 + J * kBlk + jl0;
+          const int nv = last - jl0 + 1 < 4 ? last - jl0 + 1 : 4;
+          if (nv == 4 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+            int4* d4 = reinterpret_cast<int4*>(dst);
+            int4 w0 = make_int4(v[0].x, v[0].y, v[1].x, v[1].y), w1 = make_int4(v[2].x, v[2].y, v[3].x, v[3].y);
+            if (p.accumulate) {
+              const int4 o0 = d4[0], o1 = d4[1];
+              w0 = make_int4(w0.x + o0.x, w0.y + o0.y, w0.z + o0.z, w0.w + o0.w);
+              w1 = make_int4(w1.x + o1.x, w1.y + o1.y, w1.z + o1.z, w1.w + o1.w);
+            }
+            d4[0] = w0;
+            d4[1] = w1;
+          } else {
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int i = row0 + 2 * (8 * h + r) + half;
-            if (i < p.n_inputs && j <= i) {
-              int nr, ni;
-              if (magic) {
-                nr = __float_as_int(fmaf(__uint_as_float(vr[r]), 262144.0f, kMagic));
-                ni = __float_as_int(fmaf(__uint_as_float(vi[r]), 262144.0f, kMagic));
-              } else {
-                nr = __float2int_rn(__uint_as_float(vr[r]) * 262144.0f);
-                ni = __float2int_rn(__uint_as_float(vi[r]) * 262144.0f);
+            for (int k = 0; k < 4; ++k) {
+              if (k < nv) {
+                int2 w = v[k];
+                if (p.accumulate) {
+                  const int2 o = dst[k];
+                  w.x += o.x;
+                  w.y += o.y;
+                }
+                dst[k] = w;
               }
-              int2 v = make_int2(nr + rc[r].x - s.x, -ni + rc[r].y + s.y);
-              int2* dst = out_c + (int64_t)i * (i + 1) / 2 + j;
-              if (p.accumulate) {
-                const int2 o = *dst;
-                v.x += o.x;
-                v.y += o.y;
-              }
-              *dst = v;
             }
           }
         }
