@@ -296,13 +296,16 @@ xcorr_status xcorr_correlate_ci4_noalloc(const void *d_in, int n_time, int n_cha
 /*
  * Batches: many independent 4-bit correlations of uneven size (each its own
  * station count, channel count and integration length; Sec. 2.1: each
- * sub-band is an independent X-stage) in one persistent tensor-core launch.
- * Each execute unpacks every subarray, then runs one X launch over the union
- * of their tile pairs, longest first, so small subarrays fill the tail of the
- * large ones.  Subarray s correlates exactly cfgs[s].max_time_per_exec
+ * sub-band is an independent X-stage) in one persistent tensor-core launch
+ * over the union of their tile pairs, longest first, so small subarrays fill
+ * the tail of the large ones.  When every subarray has a multiple of 16
+ * inputs and at most 37,248 samples, the launch is the fused 4-bit kernel
+ * (A operand in tensor memory) reading d_ins directly (16-byte aligned);
+ * otherwise each execute first unpacks every subarray into staging planes the
+ * batch owns.  Subarray s correlates exactly cfgs[s].max_time_per_exec
  * (<= 130,944) samples per execute from d_ins[s] ([t][c][s][2] CI4, device)
- * into d_outs[s] (int32 [C][P][2], device, written, not added to).
- * The batch owns each subarray's staging planes; the caller owns the buffers.
+ * into d_outs[s] (int32 [C][P][2], device, written, not added to).  The
+ * caller owns the buffers.
  */
 typedef struct xcorr_batch_s *xcorr_batch;
 
@@ -311,10 +314,14 @@ typedef struct xcorr_batch_s *xcorr_batch;
  * smallest nonzero hbm_budget_bytes), OOM, CUDA. */
 xcorr_status xcorr_batch_create(xcorr_batch *out, const xcorr_config *cfgs, int n);
 
-/* The stage ring of the batch launch (0, 1 or 2 as in xcorr_tuning). */
+/* The launch shape: 0, 1, 2 for the planes path's rings (as in xcorr_tuning),
+ * 3, 4, 5 for the fused kernel's (as xcorr_tuning's 4, 5, 6; 3 is the default
+ * of a batch that qualifies).  Errors: INVALID_ARG, UNSUPPORTED (a fused shape
+ * for a batch that does not qualify), OOM (the planes of a planes shape). */
 xcorr_status xcorr_batch_set_variant(xcorr_batch batch, int stage_variant);
 
-/* One batch execute on the stream.  Errors: INVALID_ARG, CUDA. */
+/* One batch execute on the stream.  Errors: INVALID_ARG (a NULL buffer, or an
+ * input the fused kernel cannot read: not 16-byte aligned), CUDA. */
 xcorr_status xcorr_batch_execute(xcorr_batch batch, const void *const *d_ins, void *const *d_outs,
                                  void *stream);
 

@@ -2,13 +2,18 @@
 // persistent tensor-core launch, optionally replayed as a CUDA graph.
 //
 // A batch holds n subarrays (each its own station count, channel count and
-// integration length, 4+4-bit input).  One execute unpacks every subarray
-// into its own E4M3 planes and then runs a single launch of the X kernel over
-// the union of their work items (subarray, channel, I, J), sorted longest
-// first and dealt round-robin to the persistent CTAs, so a large subarray's
-// tail is filled with the small ones' items instead of leaving SMs idle
-// between per-instance launches.  Sec. 2.1: each sub-band (here each
-// subarray) is an independent X-stage.
+// integration length, 4+4-bit input).  One execute runs a single launch of an
+// X kernel over the union of their work items (subarray, channel, I, J),
+// sorted longest first and dealt round-robin to the persistent CTAs, so a
+// large subarray's tail is filled with the small ones' items instead of
+// leaving SMs idle between per-instance launches.  Sec. 2.1: each sub-band
+// (here each subarray) is an independent X-stage.
+//
+// Stage variants 3-5 (the default when every subarray has a multiple of 16
+// inputs and fits one exactly-summed block) run the fused 4-bit kernel with
+// the A operand in tensor memory straight on the callers' raw inputs; 0-2
+// first unpack every subarray into its own E4M3 planes and run the planes
+// kernel.
 #include <algorithm>
 #include <new>
 #include <string>
@@ -19,7 +24,12 @@
 struct xcorr_batch_s {
   int n = 0;
   int device = 0, num_sms = 0;
-  int variant = 0;
+  int variant = 0;              // 0-2 planes path, 3-5 fused kernel (its variants 0-2)
+  bool fusable = false;         // every subarray qualifies for the fused kernel
+  xc::TaSubDesc* fdescs_host = nullptr;  // fused descriptors (pinned), n entries
+  xc::TaSubDesc* fdescs_dev = nullptr;
+  std::vector<const void*> ins;  // the inputs the fused descriptors were built for
+  int built_variant = -1;        // the variant the device tables hold
   std::vector<xcorr_config> cfg;
   std::vector<int> n_inputs, ni_pad;
   std::vector<int64_t> n_pairs;
@@ -43,36 +53,74 @@ void batch_release(xcorr_batch b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (void* p : b->planes)
     if (p) cudaFree(p);
+  if (b->fdescs_dev) cudaFree(b->fdescs_dev);
+  if (b->fdescs_host) cudaFreeHost(b->fdescs_host);
   if (b->descs_dev) cudaFree(b->descs_dev);
   if (b->items_dev) cudaFree(b->items_dev);
   if (b->descs_host) cudaFreeHost(b->descs_host);
   if (b->status) cudaFree(b->status);
 }
 
-// (Re)build the subarray descriptors and the item list for stage variant v
-// and the given output buffers.
-xcorr_status build_tables(xcorr_batch b, void* const* d_outs) {
-  const int kt = xc::tc_stage_samples(1, b->variant);
+constexpr int kFusedBase = xc::kTcVariants;  // batch variants kFusedBase + v run the fused kernel's variant v
+
+bool fused_mode(const xcorr_batch_s* b) { return b->variant >= kFusedBase; }
+
+// The planes path's staging planes, allocated when a planes variant is first chosen.
+xcorr_status ensure_planes(xcorr_batch b) {
+  for (int s = 0; s < b->n; ++s) {
+    if (b->planes[s]) continue;
+    const xcorr_config& c = b->cfg[s];
+    cudaError_t e = cudaMalloc(&b->planes[s], (size_t)c.n_channels * 2 * c.max_time_per_exec * b->ni_pad[s]);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return bfail(XCORR_ERR_OOM, std::string("batch planes: ") + cudaGetErrorString(e));
+    }
+  }
+  return XCORR_OK;
+}
+
+// (Re)build the subarray descriptors and the item list for the batch's variant and the given
+// inputs (the fused kernel reads them through its tensor maps) and outputs.
+xcorr_status build_tables(xcorr_batch b, const void* const* d_ins, void* const* d_outs) {
+  const bool fused = fused_mode(b);
+  const int kt = fused ? xc::fused_ta_stage_samples(b->variant - kFusedBase) : xc::tc_stage_samples(1, b->variant);
   std::vector<uint4> items;
   std::vector<int> cost;
   for (int s = 0; s < b->n; ++s) {
     const int n_time = b->cfg[s].max_time_per_exec;
-    std::string err;
-    if (!xc::encode_plane_tmap(&b->descs_host[s].tmap, b->planes[s], 1, b->n_inputs[s], b->ni_pad[s], n_time, n_time,
-                               2 * b->cfg[s].n_channels, kt, &err))
-      return bfail(XCORR_ERR_CUDA, err);
-    xc::SubDescHost& d = b->descs_host[s];
-    d.out = d_outs ? d_outs[s] : nullptr;
-    d.n_pairs = b->n_pairs[s];
-    d.n_inputs = b->n_inputs[s];
-    d.n_kt = (n_time + kt - 1) / kt;
-    d.n_tw = (d.n_kt + xc::kTcWindowCI4 / kt - 1) / (xc::kTcWindowCI4 / kt);
+    const int C = b->cfg[s].n_channels;
     const int nb = (b->n_inputs[s] + 127) / 128;
-    for (int c = 0; c < b->cfg[s].n_channels; ++c)
+    std::string err;
+    int n_kt;
+    if (fused) {
+      xc::TaSubDesc& d = b->fdescs_host[s];
+      if (d_ins && !xc::encode_raw_ci4_tmap(&d.tmap, d_ins[s], b->n_inputs[s], C, C, n_time, kt, &err))
+        return bfail(XCORR_ERR_INVALID_ARG, "subarray " + std::to_string(s) + ": " + err);
+      d.out = d_outs ? static_cast<int2*>(d_outs[s]) : nullptr;
+      d.n_pairs = b->n_pairs[s];
+      d.n_inputs = b->n_inputs[s];
+      d.n_tile_pairs = nb * (nb + 1) / 2;
+      d.n_kt = (n_time + kt - 1) / kt;
+      d.accumulate = 0;
+      n_kt = d.n_kt;
+      b->ins[s] = d_ins ? d_ins[s] : nullptr;
+    } else {
+      if (!xc::encode_plane_tmap(&b->descs_host[s].tmap, b->planes[s], 1, b->n_inputs[s], b->ni_pad[s], n_time,
+                                 n_time, 2 * C, kt, &err))
+        return bfail(XCORR_ERR_CUDA, err);
+      xc::SubDescHost& d = b->descs_host[s];
+      d.out = d_outs ? d_outs[s] : nullptr;
+      d.n_pairs = b->n_pairs[s];
+      d.n_inputs = b->n_inputs[s];
+      d.n_kt = (n_time + kt - 1) / kt;
+      d.n_tw = (d.n_kt + xc::kTcWindowCI4 / kt - 1) / (xc::kTcWindowCI4 / kt);
+      n_kt = d.n_kt;
+    }
+    for (int c = 0; c < C; ++c)
       for (int I = 0; I < nb; ++I)
         for (int J = 0; J <= I; ++J) {
           items.push_back(make_uint4((unsigned)s, (unsigned)c, (unsigned)I, (unsigned)J));
-          cost.push_back(d.n_kt);
+          cost.push_back(n_kt);
         }
   }
   // longest first: a stable sort keeps each subarray's items channel-major
@@ -91,15 +139,23 @@ xcorr_status build_tables(xcorr_batch b, void* const* d_outs) {
   b->n_items = (int)sorted.size();
   if ((e = cudaMemcpy(b->items_dev, sorted.data(), sorted.size() * sizeof(uint4), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
-      (e = cudaMemcpy(b->descs_dev, b->descs_host, sizeof(xc::SubDescHost) * b->n, cudaMemcpyHostToDevice)) !=
-          cudaSuccess)
+      (fused ? (e = cudaMemcpy(b->fdescs_dev, b->fdescs_host, sizeof(xc::TaSubDesc) * b->n, cudaMemcpyHostToDevice))
+             : (e = cudaMemcpy(b->descs_dev, b->descs_host, sizeof(xc::SubDescHost) * b->n,
+                               cudaMemcpyHostToDevice))) != cudaSuccess)
     return bfail(XCORR_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
+  b->built_variant = b->variant;
   return XCORR_OK;
 }
 
-// Enqueue one batch execute: every unpack, then one X launch.
+// Enqueue one batch execute: one fused launch, or every unpack and then one X launch.
 xcorr_status enqueue(xcorr_batch b, const void* const* d_ins, cudaStream_t s) {
   cudaError_t e;
+  if (fused_mode(b)) {
+    e = xc::launch_xcorr_tc_fused_ta_batch(b->fdescs_dev, b->items_dev, b->n_items, b->variant - kFusedBase,
+                                           b->status, b->num_sms, s);
+    if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("fused batch launch: ") + cudaGetErrorString(e));
+    return XCORR_OK;
+  }
   for (int k = 0; k < b->n; ++k) {
     e = xc::launch_unpack_ci4_e4m3(static_cast<const uint8_t*>(d_ins[k]), static_cast<uint8_t*>(b->planes[k]),
                                    b->cfg[k].max_time_per_exec, b->cfg[k].n_channels, b->n_inputs[k], b->ni_pad[k],
@@ -143,6 +199,7 @@ xcorr_status xcorr_batch_create(xcorr_batch* out, const xcorr_config* cfgs, int 
   b->num_sms = sms;
   b->cfg.assign(cfgs, cfgs + n);
   size_t budget = 0, need = 0;
+  b->fusable = true;
   for (int s = 0; s < n; ++s) {
     const int ni = 2 * cfgs[s].n_stations;
     b->n_inputs.push_back(ni);
@@ -150,15 +207,21 @@ xcorr_status xcorr_batch_create(xcorr_batch* out, const xcorr_config* cfgs, int 
     b->n_pairs.push_back((int64_t)ni * (ni + 1) / 2);
     need += (size_t)cfgs[s].n_channels * 2 * cfgs[s].max_time_per_exec * b->ni_pad.back();
     if (cfgs[s].hbm_budget_bytes) budget = budget ? std::min(budget, cfgs[s].hbm_budget_bytes) : cfgs[s].hbm_budget_bytes;
+    b->fusable = b->fusable && ni % 16 == 0 && cfgs[s].max_time_per_exec <= xc::kFusedWindowCI4;
   }
-  if (budget && need > budget) {
+  // the fused kernel reads the raw inputs directly; the planes path needs its staging planes
+  b->variant = b->fusable ? kFusedBase : 0;
+  if (!b->fusable && budget && need > budget) {
     delete b;
     return bfail(XCORR_ERR_BUDGET, "the batch needs " + std::to_string(need) + " device bytes of planes, budget " +
                                        std::to_string(budget));
   }
   b->planes.assign(n, nullptr);
-  for (int s = 0; s < n && e == cudaSuccess; ++s)
+  b->ins.assign(n, nullptr);
+  for (int s = 0; s < n && e == cudaSuccess && !b->fusable; ++s)
     e = cudaMalloc(&b->planes[s], (size_t)cfgs[s].n_channels * 2 * cfgs[s].max_time_per_exec * b->ni_pad[s]);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b->fdescs_host), sizeof(xc::TaSubDesc) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->fdescs_dev, sizeof(xc::TaSubDesc) * n);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b->descs_host), sizeof(xc::SubDescHost) * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->descs_dev, sizeof(xc::SubDescHost) * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->status, 256);
@@ -170,20 +233,24 @@ xcorr_status xcorr_batch_create(xcorr_batch* out, const xcorr_config* cfgs, int 
     return bfail(e == cudaErrorMemoryAllocation ? XCORR_ERR_OOM : XCORR_ERR_CUDA,
                  std::string("batch allocation: ") + cudaGetErrorString(e));
   }
-  xcorr_status st = build_tables(b, nullptr);
-  if (st != XCORR_OK) {
-    batch_release(b);
-    delete b;
-    return st;
-  }
-  *out = b;
+  *out = b;  // the tables are built by the first execute or capture, which name the buffers
   return XCORR_OK;
 }
 
 xcorr_status xcorr_batch_set_variant(xcorr_batch b, int stage_variant) {
-  if (!b || stage_variant < 0 || stage_variant >= xc::kTcVariants)
-    return bfail(XCORR_ERR_INVALID_ARG, "need a batch and stage_variant in [0, 2]");
+  if (!b || stage_variant < 0 || stage_variant >= kFusedBase + 3)
+    return bfail(XCORR_ERR_INVALID_ARG, "need a batch and stage_variant in [0, 5]");
+  if (stage_variant >= kFusedBase && !b->fusable)
+    return bfail(XCORR_ERR_UNSUPPORTED,
+                 "the fused variants need every subarray to have a multiple of 16 inputs and at most 37,248 samples");
+  if (stage_variant < kFusedBase) {
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    xcorr_status st = ensure_planes(b);
+    if (st != XCORR_OK) return st;
+  }
   b->variant = stage_variant;
+  b->built_variant = -1;
   if (b->graph_exec) {  // a captured graph holds the old shape
     cudaGraphExecDestroy(b->graph_exec);
     cudaGraphDestroy(b->graph);
@@ -199,14 +266,14 @@ xcorr_status xcorr_batch_execute(xcorr_batch b, const void* const* d_ins, void* 
     if (!d_ins[s] || !d_outs[s]) return bfail(XCORR_ERR_INVALID_ARG, "a subarray buffer is NULL");
   cudaError_t e = cudaSetDevice(b->device);
   if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
-  // the tables are rewritten only when the outputs or the variant changed
-  bool same = true;
-  for (int s = 0; s < b->n && same; ++s) same = (b->descs_host[s].out == d_outs[s]);
-  const int kt = xc::tc_stage_samples(1, b->variant);
-  same = same && b->descs_host[0].n_kt == (b->cfg[0].max_time_per_exec + kt - 1) / kt;
+  // the tables are rewritten only when the variant or the buffers they name changed
+  const bool fused = fused_mode(b);
+  bool same = b->built_variant == b->variant;
+  for (int s = 0; s < b->n && same; ++s)
+    same = fused ? (b->fdescs_host[s].out == d_outs[s] && b->ins[s] == d_ins[s]) : (b->descs_host[s].out == d_outs[s]);
   if (!same) {
     cudaStreamSynchronize(static_cast<cudaStream_t>(stream));  // earlier launches read the tables
-    xcorr_status st = build_tables(b, d_outs);
+    xcorr_status st = build_tables(b, d_ins, d_outs);
     if (st != XCORR_OK) return st;
   }
   return enqueue(b, d_ins, static_cast<cudaStream_t>(stream));
@@ -218,7 +285,7 @@ xcorr_status xcorr_batch_capture(xcorr_batch b, const void* const* d_ins, void* 
   if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
   // (recording only: the graph runs later on whatever stream replays it)
   cudaStreamSynchronize(static_cast<cudaStream_t>(stream));  // earlier launches may still read the tables
-  xcorr_status st = build_tables(b, d_outs);
+  xcorr_status st = build_tables(b, d_ins, d_outs);
   if (st != XCORR_OK) return st;
   if (b->graph_exec) {
     cudaGraphExecDestroy(b->graph_exec);

@@ -146,6 +146,16 @@ struct SubDescHost {
   int64_t n_pairs;
   int n_inputs, n_kt, n_tw, pad;
 };
+// A subarray of a batch run by the fused 4-bit kernel (A operand in tensor memory).
+struct TaSubDesc {
+  CUtensorMap tmap;  // its raw CI4 input: boxes of 128 inputs x 1 channel x the stage height
+  int2* out;         // its int2 [C][P] visibilities
+  int64_t n_pairs;
+  int n_inputs, n_tile_pairs, n_kt, accumulate;
+};
+static_assert(sizeof(TaSubDesc) % 64 == 0, "tensor maps in a descriptor array stay 64-byte aligned");
+cudaError_t launch_xcorr_tc_fused_ta_batch(const TaSubDesc* subs, const uint4* items, int n_items, int variant,
+                                           int* status, int num_sms, cudaStream_t stream);
 // One launch of the batch X kernel over items (subarray, channel, I, J).
 cudaError_t launch_xcorr_tc_batch(const void* subs, const uint4* items, int n_items, int variant, int* status,
                                   int num_sms, cudaStream_t stream);

@@ -98,14 +98,68 @@ struct TParams {
   int2* out;
   int* status;
   uint32_t one;        // 1: a multiplier the compiler cannot fold (see lane_add)
+  // batch mode: items (subarray, channel, I, J) and one descriptor per subarray
+  const TaSubDesc* subs;
+  const uint4* items;
+  int n_batch_items;
 };
+
+// Everything a role needs of one item: its tile pair and its subarray (the launch's own problem,
+// or in batch mode the item's subarray descriptor).
+struct TItem {
+  const CUtensorMap* map;  // raw input
+  int2* out;
+  int64_t n_pairs;
+  int c, I, J, n_inputs, n_kt, accumulate;
+  bool diag, valid;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ TItem resolve(const TParams& p, const CUtensorMap* map, int item, int n_items) {
+  TItem it{};
+  it.valid = item < n_items;
+  if (!it.valid) return it;
+  if (BATCH) {
+    const uint4 w = p.items[item];
+    const TaSubDesc* s = p.subs + w.x;
+    it.map = &s->tmap;
+    it.out = s->out;
+    it.n_pairs = s->n_pairs;
+    it.n_inputs = s->n_inputs;
+    it.n_kt = s->n_kt;
+    it.accumulate = s->accumulate;
+    it.c = static_cast<int>(w.y);
+    it.I = static_cast<int>(w.z);
+    it.J = static_cast<int>(w.w);
+  } else {
+    it.map = map;
+    it.out = p.out;
+    it.n_pairs = p.n_pairs;
+    it.n_inputs = p.n_inputs;
+    it.n_kt = p.n_kt;
+    it.accumulate = p.accumulate;
+    it.c = item / p.n_tile_pairs;
+    tile_pair(item - it.c * p.n_tile_pairs, it.I, it.J);
+  }
+  it.diag = it.I == it.J;
+  return it;
+}
+
+// L2 prefetch of stage s (KT samples from t0 + s KT) of an item: one box per tile.
+template <int KT>
+__device__ __forceinline__ void prefetch_item_stage(const TItem& it, int t0, int s) {
+  if (!it.valid || s >= it.n_kt) return;
+  const int t = t0 + s * KT;
+  tma_prefetch_3d(it.map, it.I * kBlk, it.c, t);
+  if (!it.diag) tma_prefetch_3d(it.map, it.J * kBlk, it.c, t);
+}
 
 // 16-byte chunk swizzle of the Re staging tile: a bijection of row % 8, so the eight rows of a
 // phase-1 quarter-warp store hit eight distinct chunks, and rows 2k, 2k + 1 (the two half-warps
 // of a phase-2 load) land in opposite halves of each eight-chunk group.
 __device__ __forceinline__ int staging_swizzle(int row) { return ((row & 1) << 2) | ((row >> 1) & 3); }
 
-template <int KT, int RAW, int DEC>
+template <int KT, int RAW, int DEC, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
     xcorr_tc_fused_ta_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ TParams p) {
   using G = TGeom<KT, RAW, DEC>;
@@ -155,36 +209,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int n_items = p.n_chan * p.n_tile_pairs;
+  const int n_items = BATCH ? p.n_batch_items : p.n_chan * p.n_tile_pairs;
+  const int t0 = BATCH ? 0 : p.t0;
 
   if (warp == kProducerWarp) {
     if (lane == 0) {
       constexpr int kAhead = kPrefetchSamples / KT;  // L2 prefetch runs this many stages ahead of the loads
-      prefetch_tmap(&raw_map);
-      {
-        const Item first = item_at(p.n_tile_pairs, blockIdx.x, n_items);
-        for (int s = 0; s < kAhead; ++s) prefetch_stage<KT>(&raw_map, p.t0, p.n_kt, first, s);
-      }
+      if (!BATCH) prefetch_tmap(&raw_map);
+      TItem next = resolve<BATCH>(p, &raw_map, blockIdx.x, n_items);
+      if (BATCH && next.valid) prefetch_tmap(next.map);
+      for (int s = 0; s < kAhead; ++s) prefetch_item_stage<KT>(next, t0, s);
       int r = 0;
       uint32_t ph = 0, filled = 0, fill_parity[RAW] = {};
       bool ok = true;
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-        const Item it = item_at(p.n_tile_pairs, item, n_items);
-        for (int tb = 0; tb < p.n_kt; ++tb) {
-          if (tb + kAhead < p.n_kt)
-            prefetch_stage<KT>(&raw_map, p.t0, p.n_kt, it, tb + kAhead);
+        const TItem it = next;
+        next = resolve<BATCH>(p, &raw_map, item + gridDim.x, n_items);
+        if (BATCH && next.valid) prefetch_tmap(next.map);
+        for (int tb = 0; tb < it.n_kt; ++tb) {
+          if (tb + kAhead < it.n_kt)
+            prefetch_item_stage<KT>(it, t0, tb + kAhead);
           else
-            prefetch_stage<KT>(&raw_map, p.t0, p.n_kt, item_at(p.n_tile_pairs, item + gridDim.x, n_items),
-                               tb + kAhead - p.n_kt);
+            prefetch_item_stage<KT>(next, t0, tb + kAhead - it.n_kt);
           if (!mbar_wait(&raw_empty[r], ph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
             ok = false;
             break;
           }
           uint8_t* st = raw + r * G::kRawStage;
-          const int t = p.t0 + tb * KT;
+          const int t = t0 + tb * KT;
           mbar_expect_tx(&raw_full[r], (it.diag ? 1 : 2) * G::kTile);
-          tma_load_3d(st, &raw_map, &raw_full[r], it.I * kBlk, it.c, t);
-          if (!it.diag) tma_load_3d(st + G::kTile, &raw_map, &raw_full[r], it.J * kBlk, it.c, t);
+          tma_load_3d(st, it.map, &raw_full[r], it.I * kBlk, it.c, t);
+          if (!it.diag) tma_load_3d(st + G::kTile, it.map, &raw_full[r], it.J * kBlk, it.c, t);
           fill_parity[r] = ph;
           filled |= 1u << r;
           if (++r == RAW) {
@@ -211,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int r = 0, d = 0, g = 0;
     uint32_t rph = 0, dph = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
-      const Item cur = item_at(p.n_tile_pairs, item, n_items);
+      const TItem cur = resolve<BATCH>(p, &raw_map, item, n_items);
       // A sums: inputs 16 ib + lane / 4 (0) and + 8 (1), over samples 4 (lane % 4) .. + 3 of every 16
       uint32_t sar0 = 0u, sai0 = 0u, sar1 = 0u, sai1 = 0u;
       // B sums in 16-bit lanes: word e / 2, half e % 2 holds input e of chunk L
@@ -219,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int q = 0; q < 8; ++q) s_re[q] = s_im[q] = 0u;
       bool ok = true;
-      for (int tb = 0; tb < p.n_kt; ++tb) {
+      for (int tb = 0; tb < cur.n_kt; ++tb) {
         if (!mbar_wait_warp(&raw_full[r], rph, abort_flag, p.status, DEV_TIMEOUT_FULL) ||
             !mbar_wait_warp(&dec_empty[d], dph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
           ok = false;
@@ -363,7 +418,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        for (int tb = 0; tb < p.n_kt; ++tb) {
+        const int n_kt = resolve<BATCH>(p, &raw_map, item, n_items).n_kt;
+        for (int tb = 0; tb < n_kt; ++tb) {
           if (!mbar_wait(&dec_full[d], dph, abort_flag, p.status, DEV_TIMEOUT_FULL)) {
             ok = false;
             break;
@@ -400,23 +456,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     // converts, applies the offset corrections and writes the rows; Im goes through the warp's
     // transpose buffer so that four threads write 16 consecutive pairs of one row.
     const int r_own = warp * 32 + lane;  // this thread's tile row in phase 1
-    const int t128 = 128 * p.n_kt * KT;  // 128 T over the padded block (padding decodes to u = 8 + 8i)
-    const bool magic = t128 <= 128 * kMagicSamples;
     const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     uint32_t* tim = transpose + warp * 32 * kTPitch;
     int g = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
-      const int c = item / p.n_tile_pairs;
-      int I, J;
-      tile_pair(item - c * p.n_tile_pairs, I, J);
-      int2* out_c = p.out + (int64_t)c * p.n_pairs;
+      const TItem it = resolve<BATCH>(p, &raw_map, item, n_items);
+      const int c = it.c, I = it.I, J = it.J, n_inputs = it.n_inputs;
+      const int t128 = 128 * it.n_kt * KT;  // 128 T over the padded block (padding decodes to u = 8 + 8i)
+      const bool magic = t128 <= 128 * kMagicSamples;
+      int2* out_c = it.out + (int64_t)c * it.n_pairs;
       const int row0 = I * kBlk + warp * 32;
       const int buf = g & 1;
-      if (p.accumulate) {
+      if (it.accumulate) {
         // the sums this tile pair adds to, pulled into L2 while its MMAs run: each thread
         // prefetches the 128-byte lines of its own row's segment (pairs J*128 .. min(J*128 + 127, i))
         const int i = I * kBlk + r_own;
-        if (i < p.n_inputs) {
+        if (i < n_inputs) {
           const char* a = reinterpret_cast<const char*>(out_c + (int64_t)i * (i + 1) / 2 + J * kBlk);
           const char* e = a + 8 * ((I == J ? r_own : kBlk - 1) + 1);
           for (const char* l = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(a) & ~uintptr_t(127)); l < e;
@@ -429,7 +484,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       tc_fence_after();
       // 16-pair chunks this warp keeps: none past the inputs, none wholly above the diagonal
-      const int n_ch = row0 >= p.n_inputs ? 0 : I == J ? (warp * 32 + 31) / kChunk + 1 : kBlk / kChunk;
+      const int n_ch = row0 >= n_inputs ? 0 : I == J ? (warp * 32 + 31) / kChunk + 1 : kBlk / kChunk;
       {
         uint4* srow = reinterpret_cast<uint4*>(staging + r_own * kBlk);
         const int sw = staging_swizzle(r_own);
@@ -469,10 +524,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = 0; k < kChunk / 4; ++k) trow[k] = make_uint4(im[4 * k], im[4 * k + 1], im[4 * k + 2], im[4 * k + 3]);
         __syncwarp();
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-          const int rl = 8 * it + rg, rr = warp * 32 + rl, i = I * kBlk + rr;
+        for (int rw = 0; rw < 4; ++rw) {
+          const int rl = 8 * rw + rg, rr = warp * 32 + rl, i = I * kBlk + rr;
           const int last = I == J ? rr : kBlk - 1;  // last column of the row in the tile
-          if (i >= p.n_inputs || jl0 > last) continue;
+          if (i >= n_inputs || jl0 > last) continue;
           const uint4 re4 =
               *reinterpret_cast<const uint4*>(staging + rr * kBlk + (((jl0 >> 2) ^ staging_swizzle(rr)) << 2));
           const uint4 im4 = *reinterpret_cast<const uint4*>(tim + rl * kTPitch + 4 * q4);
@@ -497,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (nv == 4 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
             int4* d4 = reinterpret_cast<int4*>(dst);
             int4 w0 = make_int4(v[0].x, v[0].y, v[1].x, v[1].y), w1 = make_int4(v[2].x, v[2].y, v[3].x, v[3].y);
-            if (p.accumulate) {
+            if (it.accumulate) {
               const int4 o0 = d4[0], o1 = d4[1];
               w0 = make_int4(w0.x + o0.x, w0.y + o0.y, w0.z + o0.z, w0.w + o0.w);
               w1 = make_int4(w1.x + o1.x, w1.y + o1.y, w1.z + o1.z, w1.w + o1.w);
@@ -509,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int k = 0; k < 4; ++k) {
               if (k < nv) {
                 int2 w = v[k];
-                if (p.accumulate) {
+                if (it.accumulate) {
                   const int2 o = dst[k];
                   w.x += o.x;
                   w.y += o.y;
@@ -535,10 +590,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int KT, int RAW, int DEC>
+template <int KT, int RAW, int DEC, bool BATCH = false>
 cudaError_t launch_ta(const CUtensorMap& raw_map, const TParams& p, int grid, cudaStream_t stream) {
   using G = TGeom<KT, RAW, DEC>;
-  auto kern = xcorr_tc_fused_ta_kernel<KT, RAW, DEC>;
+  auto kern = xcorr_tc_fused_ta_kernel<KT, RAW, DEC, BATCH>;
   static int attr_device = -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -593,6 +648,31 @@ cudaError_t launch_xcorr_tc_fused_ta_ci4(const uint8_t* in, int row_chans, int v
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+}  // namespace xc
+
+namespace xc {
+
+// The batch form: one launch over items (subarray, channel, I, J) of several 4-bit problems, each
+// with its own descriptor (raw tensor map with box_t = the variant's stage height, output, sizes;
+// one exactly-summed block each: n_kt * KT <= kFusedWindowCI4).
+cudaError_t launch_xcorr_tc_fused_ta_batch(const TaSubDesc* subs, const uint4* items, int n_items, int variant,
+                                           int* status, int num_sms, cudaStream_t stream) {
+  if (n_items <= 0) return cudaSuccess;
+  TParams p{};
+  p.status = status;
+  p.one = 1u;
+  p.subs = subs;
+  p.items = items;
+  p.n_batch_items = n_items;
+  CUtensorMap unused{};
+  const int grid = n_items < num_sms ? n_items : num_sms;
+  switch (variant) {
+    case 0: return launch_ta<128, 2, 2, true>(unused, p, grid, stream);
+    case 1: return launch_ta<96, 3, 2, true>(unused, p, grid, stream);
+    default: return launch_ta<64, 4, 4, true>(unused, p, grid, stream);
+  }
 }
 
 }  // namespace xc

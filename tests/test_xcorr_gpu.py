@@ -447,6 +447,47 @@ def test_batch_graph_replay(torch):
             assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, y))
 
 
+# every input count a multiple of 16 (ragged 128-input tiles at 144, 400, 272), time tails
+FUSABLE = [(8, 3, 512), (72, 2, 200), (200, 1, 385), (24, 4, 33), (136, 2, 1024), (256, 1, 96)]
+
+
+@pytest.mark.parametrize("variant", [3, 4, 5])
+def test_fused_batch_bit_exact(torch, variant):
+    xs = batch_inputs(FUSABLE, 300 + variant)
+    with xcorr.Batch(FUSABLE) as batch:
+        batch.set_variant(variant)
+        outs = batch.execute([torch.from_numpy(x).cuda() for x in xs])
+        batch.sync()
+        for x, o in zip(xs, outs):
+            assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, x))
+
+
+def test_fused_batch_is_the_default_and_replays_new_data(torch):
+    sizes = FUSABLE[:4]
+    xs, ys = batch_inputs(sizes, 41), batch_inputs(sizes, 42)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    with xcorr.Batch(sizes) as batch:
+        batch.capture(xd)
+        outs = batch.replay()
+        batch.sync()
+        for x, o in zip(xs, outs):
+            assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, x))
+        for dst, y in zip(xd, ys):  # the fused kernel reads the inputs in place
+            dst.copy_(torch.from_numpy(y).cuda())
+        outs = batch.replay()
+        batch.sync()
+        for y, o in zip(ys, outs):
+            assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, y))
+
+
+def test_fused_shapes_refused_for_batches_they_do_not_fit(torch):
+    with xcorr.Batch([(70, 2, 200)]) as batch:  # 140 inputs: not a multiple of 16
+        with pytest.raises(xcorr.XcorrError) as e:
+            batch.set_variant(3)
+        assert e.value.status == 2  # UNSUPPORTED
+        batch.set_variant(0)
+
+
 def test_batch_rejects_what_it_does_not_serve(torch):
     with pytest.raises(xcorr.XcorrError):
         xcorr.Batch([(8, 2, 200000)])  # more than one window per execute
