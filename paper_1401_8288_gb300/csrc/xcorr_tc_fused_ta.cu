@@ -20,24 +20,27 @@
 //   * per 32-sample step the MMAs are Re|-Im += A_re [B_re | B_im],
 //     Re += A_im B_im, -Im += -A_im B_re, A read from tensor memory.
 //
-// Tensor memory holds the accumulator [Re | -Im] in columns 0-255 and DEC A
-// stages (real then imaginary codes, KT / 2 columns) in columns 256-511, so
-// the accumulator is single-buffered.  The epilogue therefore frees it in one
-// quick pass, converting and correcting into a shared-memory tile of the whole
-// tile pair (128 x 128 int32 pairs), and writes that tile to HBM while the
-// MMAs already run the next tile pair; the decoders keep filling the rings in
-// the meantime.
+// Tensor memory holds the accumulator [Re | -Im] in columns 0-255, a stash
+// for Im in columns 256-383 and DEC A stages (real then imaginary codes,
+// KT / 2 columns) from column 384, so the accumulator is single-buffered.  The
+// epilogue therefore frees it in one quick pass that only moves bits: Re to a
+// shared-memory tile of the whole tile pair, Im to the stash.  While the MMAs
+// already run the next tile pair it converts (one FFMA against 1.5 2^23 while
+// the block's sums stay below 2^22), applies the offset corrections and
+// writes the rows to HBM; the decoders keep filling the rings meanwhile.
 //
 // The per-input sums S = sum_t u that undo the offset (see xcorr_tc_fused.cu)
 // come from the A path for the rows (dp4a over the codes each thread holds)
 // and from the B path for the columns (byte lanes, as in the other kernel).
 //
 // Warp roles (448 threads, one CTA per SM): warps 0-3 drain the accumulator
-// and write the output;
-// warps 4-11 decode (warp w writes the A lanes of TMEM quarter w % 4, 16
-// inputs, and a share of B); warp 12 is the TMA producer with the L2
-// prefetch; warp 13 owns tensor memory and issues the MMAs.  Every wait is
-// bounded (sm103_ptx.cuh).
+// and write the output; warps 4-11 decode (warp w writes the A lanes of TMEM
+// quarter w % 4, 16 inputs, and a share of B); warp 12 is the TMA producer
+// with the L2 prefetch; warp 13 owns tensor memory and issues the MMAs.
+// Every wait is bounded (sm103_ptx.cuh).
+//
+// A batch mode (xcorr_batch.cu) runs the same pipeline over the tile pairs of
+// several problems, each item naming its problem's descriptor.
 #include "fused_common.cuh"
 #include "sm103_ptx.cuh"
 #include "xcorr_internal.h"
