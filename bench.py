@@ -63,11 +63,13 @@ WORKLOADS = {
 WORKLOAD = WORKLOADS["ci4_512in"]
 # ncu DRAM traffic of the headline kernel per launch, stored beside the source hash it was taken on
 KERNEL_SOURCES = {
+    "xcorr_tc_fused_pair_kernel": ("xcorr_tc_fused_pair.cu", "fused_common.cuh", "sm103_ptx.cuh", "xcorr_internal.h"),
     "xcorr_tc_fused_ta_kernel": ("xcorr_tc_fused_ta.cu", "fused_common.cuh", "sm103_ptx.cuh", "xcorr_internal.h"),
     "xcorr_tc_fused_kernel": ("xcorr_tc_fused.cu", "fused_common.cuh", "sm103_ptx.cuh", "xcorr_internal.h"),
     "xcorr_tc_kernel": ("xcorr_tc.cu", "sm103_ptx.cuh", "xcorr_internal.h"),
 }
 FUSED_TA_VARIANTS = (4, 5, 6)  # tuning stage_variants served by the tensor-memory-A fused kernel
+FUSED_PAIR_VARIANTS = (7, 8, 9)  # ... and by the CTA-pair kernel
 
 
 def profile_summary_path(kernel: str) -> str:
@@ -412,7 +414,9 @@ def our_arm(args) -> int:
     launches_per_step = plan.query()["kernels_per_execute"]  # all launches of one execute
     fused = fmt == "ci4" and tuning["unfused"] == 0
     fused_ta = fused and tuning["stage_variant"] in FUSED_TA_VARIANTS
-    x_kernel = ("xcorr_tc_fused_ta_kernel" if fused_ta else "xcorr_tc_fused_kernel") if fused else "xcorr_tc_kernel"
+    fused_pair = fused and tuning["stage_variant"] in FUSED_PAIR_VARIANTS
+    x_kernel = (("xcorr_tc_fused_pair_kernel" if fused_pair else "xcorr_tc_fused_ta_kernel" if fused_ta
+                 else "xcorr_tc_fused_kernel") if fused else "xcorr_tc_kernel")
     x_launches = launches_per_step if fused else launches_per_step // 2  # else unpack + X per channel group
     out_dtype = torch.float32 if fmt == "cf32" else torch.int32
     out = torch.empty((n_chan, n_pairs, 2), dtype=out_dtype, device=dev)
@@ -518,7 +522,13 @@ def our_arm(args) -> int:
                              "uniform": "4+4-bit complex, uniform integers in [-7, 7]",
                              "gauss8": "int8 complex, Gaussian sigma 20 clipped to +-127",
                              "gauss32": "float32 complex, Gaussian sigma 1"}[w["gen"]],
-                   "engine": {"ci4": ("tcgen05 kind::f8f6f4, unpack fused on chip, A operand decoded "
+                   "engine": {"ci4": ("tcgen05 kind::f8f6f4 cta_group::2 on SM pairs (cluster of 2) "
+                                      "sharing a column tile, M = 256: each SM decodes its row tile "
+                                      "into tensor memory (ldmatrix.trans + tcgen05.st) and half of "
+                                      "the column tile into shared memory (offset-binary E4M3 codes "
+                                      "u = t + 8, exact FP32 TMEM sums, per-input sum correction, "
+                                      "int32 out)") if fused_pair else
+                                     ("tcgen05 kind::f8f6f4, unpack fused on chip, A operand decoded "
                                       "into tensor memory (ldmatrix.trans + tcgen05.st), B in shared "
                                       "memory (offset-binary E4M3 codes u = t + 8, exact FP32 TMEM "
                                       "sums, per-input sum correction, int32 out)") if fused_ta else

@@ -90,7 +90,7 @@ typedef struct xcorr_plan_s *xcorr_plan;
 
 /* Launch shape of the tensor-core path (xcorr_plan_set_tuning, xcorr_autotune). */
 typedef struct {
-    int stage_variant;  /* shared-memory ring, 0 .. 6: planes path 0 = 3 x 64 KB, 1 (and 3 .. 6)
+    int stage_variant;  /* shared-memory ring, 0 .. 9: planes path 0 = 3 x 64 KB, 1 (and 3 .. 9)
                            = 4 x 48 KB, 2 = 6 x 32 KB stages; fused path see `unfused`         */
     int groups;         /* channel groups whose unpack overlaps the X kernel; 0 = automatic (<= 8) */
     int x_streams;      /* 1 or 2 streams the groups' X launches alternate over                 */
@@ -101,7 +101,9 @@ typedef struct {
                            operands decoded into shared memory); 4 .. 6: the A operand
                            decoded into tensor memory, raw / decoded rings of
                            128 x (2 + 2), 96 x (3 + 2), 64 x (4 + 4) samples (4 is the
-                           default of a 4-bit plan);
+                           default of a 4-bit plan); 7 .. 9: pairs of SMs (a thread-block
+                           cluster of 2, one cta_group::2 MMA) sharing a column tile,
+                           rings of 128 x (3 + 2), 128 x (4 + 2), 64 x (6 + 4) samples;
                            1 = always through E4M3 planes in HBM                            */
 } xcorr_tuning;
 
@@ -216,7 +218,7 @@ xcorr_status xcorr_watchdog_selftest(xcorr_plan plan, void *stream);
 
 /*
  * Fix the tensor path's launch shape (results do not depend on it).
- * Errors: INVALID_ARG (stage_variant not in [0, 6], groups not in [0, 8],
+ * Errors: INVALID_ARG (stage_variant not in [0, 9], groups not in [0, 8],
  * x_streams not 1 or 2), DEVICE.
  */
 xcorr_status xcorr_plan_set_tuning(xcorr_plan plan, const xcorr_tuning *tuning);

@@ -31,7 +31,7 @@ constexpr int kTcWindowBF16 = 384;
 // stays below 2^24 for T <= 37,282; rounded down to a multiple of 384 (every stage height).
 constexpr int kFusedWindowCI4 = 37248;
 constexpr int kTcVariants = 3;     // planes-path stage shapes: 64 KB x 3, 48 KB x 4, 32 KB x 6
-constexpr int kFusedVariants = 7;  // fused 4-bit kernel shapes (the tuning's stage_variant range)
+constexpr int kFusedVariants = 10;  // fused 4-bit kernel shapes (the tuning's stage_variant range)
 constexpr int kDefaultFusedVariant = 4;  // 4-bit plans before any tuning: A in tensor memory, 128 x (2 + 2)
 // The planes path's shape for a tuning's stage_variant (3 exists only for the fused kernel).
 inline int planes_variant(int v) { return v >= kTcVariants ? 1 : v; }
@@ -189,17 +189,19 @@ bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inp
 
 // Tensor map over n_chan channels of a CI4 input [t][c][i] whose time rows hold
 // row_chans channels (n_inputs % 16 == 0, 16-byte aligned pointer to the first
-// channel): boxes of 128 inputs x 1 channel x box_t samples, 128-byte swizzle
-// (the fused kernel's raw tiles, and its L2 prefetches).
+// channel): boxes of box_i (128 or 64) inputs x 1 channel x box_t samples,
+// swizzled at the box's row width (the fused kernels' raw tiles, and their L2
+// prefetches).
 bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int row_chans, int n_time,
-                         int box_t, std::string* err);
+                         int box_t, std::string* err, int box_i = 128);
 // The fused 4-bit X kernel (unpack on chip, offset-binary operands): one
 // launch per kFusedWindowCI4 samples; n_inputs % 16 == 0, `in` 16-byte aligned.
 int fused_stage_samples(int variant);
 int fused_launches(int n_time);
 // `in` points at the first of n_chan channels; time rows hold row_chans channels.
 // Variants 0-3 decode both operands into shared memory; 4-6 run the kernel
-// with the A operand in tensor memory (its variants 0-2).
+// with the A operand in tensor memory (its variants 0-2); 7-9 run the CTA-pair
+// kernel (its variants 0-2).
 cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                       int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
                                       cudaStream_t stream);
@@ -208,6 +210,13 @@ int fused_ta_stage_samples(int variant);
 cudaError_t launch_xcorr_tc_fused_ta_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                          int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
                                          cudaStream_t stream);
+
+// The fused 4-bit kernel on CTA pairs (xcorr_tc_fused_pair.cu): two SMs share
+// one column tile through a cta_group::2 MMA.
+int fused_pair_stage_samples(int variant);
+cudaError_t launch_xcorr_tc_fused_pair_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
+                                           int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
+                                           cudaStream_t stream);
 
 // int8 (re, im) samples -> two BF16 planes [c][2][t][ni_pad] (exact).
 cudaError_t launch_unpack_ci8_bf16(const int8_t* in, uint16_t* planes, int n_time, int n_chan, int c0,

@@ -143,19 +143,24 @@ bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inp
 }
 
 bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int row_chans, int n_time,
-                         int box_t, std::string* err) {
+                         int box_t, std::string* err, int box_i) {
   auto fn = encode_tiled_fn(err);
   if (!fn) return false;
   std::memset(map, 0, sizeof(*map));
+  if (box_i != 128 && box_i != 64) {
+    if (err) *err = "raw input box must be 128 or 64 inputs wide";
+    return false;
+  }
   // the caller's [t][c][i] bytes: dim0 input, dim1 channel, dim2 time; a box is
-  // 128 inputs x 1 channel x box_t samples = box_t rows of 128 bytes
+  // box_i inputs x 1 channel x box_t samples = box_t rows of box_i bytes, swizzled
+  // at the row width (128- or 64-byte pattern)
   cuuint64_t dims[3] = {(cuuint64_t)n_inputs, (cuuint64_t)n_chan, (cuuint64_t)n_time};
   cuuint64_t strides[2] = {(cuuint64_t)n_inputs, (cuuint64_t)n_inputs * (cuuint64_t)row_chans};
-  cuuint32_t box[3] = {128, 1, (cuuint32_t)box_t};
+  cuuint32_t box[3] = {(cuuint32_t)box_i, 1, (cuuint32_t)box_t};
   cuuint32_t elem_strides[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(in), dims, strides, box, elem_strides,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, box_i == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     if (err) *err = "cuTensorMapEncodeTiled (raw input) failed with CUresult " + std::to_string((int)r);
     return false;

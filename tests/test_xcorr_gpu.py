@@ -328,7 +328,7 @@ def test_every_launch_shape_is_exact(torch, variant, groups, x_streams):
     assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("n_sta,n_chan,n_time", [(8, 1, 1), (8, 2, 65), (64, 3, 300), (72, 2, 257),
                                                  (200, 2, 385), (256, 3, 1000)])
 def test_fused_4bit_kernel_bit_exact(torch, variant, n_sta, n_chan, n_time):
@@ -348,10 +348,32 @@ def test_fused_and_planes_paths_agree_over_several_executes(torch, unfused):
     assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
 
 
+@pytest.mark.parametrize("variant", [7, 8, 9])
+@pytest.mark.parametrize("n_sta,n_chan,n_time", [(288, 2, 130), (320, 1, 64), (392, 2, 200), (512, 1, 96)])
+def test_pair_kernel_every_tile_count(torch, variant, n_sta, n_chan, n_time):
+    # The CTA-pair kernel groups a channel's tile pairs by column tile: 5 tiles
+    # (15 tile pairs: one entry keeps a single, one pair is transposed), 5 full
+    # tiles, 7 tiles with a 16-input last tile (a column half wholly past the
+    # inputs), 8 tiles (two transposed tile pairs).
+    x = synth.uniform_ci4(n_time, n_chan, n_sta, seed=variant * 100 + n_sta, lo=-8, hi=7)
+    got, _ = run(torch, x, "tensor", tuning=(variant, 0, 2, 0))
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+@pytest.mark.parametrize("n_sta", [256, 392])
+def test_pair_kernel_accumulates_over_executes(torch, n_sta):
+    # later executes add into the accumulator, transposed tile pairs included
+    chunks = [96, 300, 7]
+    x = synth.uniform_ci4(sum(chunks), 2, n_sta, seed=n_sta + 1, lo=-8, hi=7)
+    got, n = run(torch, x, "tensor", chunks=chunks, tuning=(7, 0, 2, 0))
+    assert n == sum(chunks)
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
 FUSED_BLOCK = 37248  # samples per exactly-summed block of the fused kernel
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("pattern", ["max", "extremes"])
 def test_fused_exact_across_blocks_at_the_bound(torch, variant, pattern):
     # Two full blocks and a tail.  "max": every sample 7 + 7i, so each block's
@@ -398,7 +420,7 @@ def test_autotune_keeps_results_exact(torch):
     with xcorr.Plan(128, 64, 256) as plan:
         plan.execute(xd)  # an integration in progress is discarded by the autotuner
         best, ms = plan.autotune(xd)
-        assert 0 <= best["stage_variant"] <= 6 and 1 <= best["groups"] <= 8 and ms > 0
+        assert 0 <= best["stage_variant"] <= 9 and 1 <= best["groups"] <= 8 and ms > 0
         assert plan.query()["samples_integrated"] == 0
         assert plan.query()["tuning"]["stage_variant"] == best["stage_variant"]
         plan.execute(xd)
@@ -528,6 +550,7 @@ def workload_512():
     ("tensor", (1, 0, 2, 0)),   # the fused shape the benchmark's autotuner picks
     ("tensor", (0, 0, 2, 0)), ("tensor", (3, 0, 2, 0)),
     ("tensor", (4, 0, 2, 0)), ("tensor", (5, 0, 2, 0)), ("tensor", (6, 0, 2, 0)),  # A in tensor memory
+    ("tensor", (7, 0, 2, 0)), ("tensor", (8, 0, 2, 0)), ("tensor", (9, 0, 2, 0)),  # CTA pairs
     ("tensor", (0, 1, 1, 1)),   # the planes path
     ("cuda_core", None)])
 def test_workload_512_inputs_512_channels_2048_samples(torch, workload_512, engine, tuning):
