@@ -54,15 +54,14 @@ constexpr int kProducerWarp = kDecWarp0 + kDecWarps;
 constexpr int kMmaWarp = kProducerWarp + 1;
 constexpr int kThreads = (kMmaWarp + 1) * 32;
 constexpr int kDecThreads = kDecWarps * 32;
+constexpr int kDecGroups = 2;                    // decoder groups taking alternate stages
+constexpr int kGroupWarps = kDecWarps / kDecGroups;  // one warp per tensor-memory lane quarter
 constexpr int kChunk = 16;
 constexpr int kPitch = kChunk + 1;
 constexpr int kHalf = 64;                                 // column-tile inputs each CTA decodes
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kStashCol = 256;                       // Im of tile columns 0-63 after the accumulator
-constexpr int kStashChunks = 4;                           // (16-column chunks; columns 64-127 go to shared memory)
-constexpr uint32_t kAcol0 = kStashCol + kStashChunks * 16;  // then the A stages
+constexpr uint32_t kStashCol = 256;                       // Im of the first STASH column chunks after the accumulator
 constexpr int kStagingBytes = kBlk * kBlk * 4;            // Re accumulator bits of a whole tile pair
-constexpr int kImHiBytes = kBlk * (kBlk - 16 * kStashChunks) * 4;  // Im bits of tile columns 64-127
 constexpr int kTPitch = 20;                               // Im transpose rows: 16 words + 16 bytes of pad
 constexpr int kTransposeBytes = kEpiWarps * 32 * kTPitch * 4;
 constexpr int kRowcBytes = kBlk * 8;                      // per-row correction constants
@@ -74,27 +73,37 @@ constexpr int kMagicSamples = 9320;
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 constexpr int kScratchBytes = kDecWarps * 4 * kPitch * 8;  // [decoder warp][chunk][input] (P, Q), padded rows
+constexpr int kRscratchBytes = kBlk * 8;                   // the second decoder group's row sums
 constexpr int kBarrierBytes = 512;
 // The odd CTA signals the even one with 16-byte copies of a token into per-warp sink slots:
 // one per decoder warp and stage, one per epilogue warp and item.
 constexpr int kSinkSlots = kDecWarps + kEpiWarps;
 constexpr uint32_t kSignalBytes = 16;
 
-template <int KT, int RAW, int DEC>
+// STASH: 16-column chunks of Im kept in tensor memory after the accumulator (the rest of Im goes to
+// shared memory); the A stages follow the stash.
+template <int KT, int RAW, int DEC, int STASH>
 struct PGeom {
+  static constexpr uint32_t kAcol0 = kStashCol + 16 * STASH;
+  static constexpr int kImHiCols = kBlk - 16 * STASH;       // Im columns staged in shared memory
+  static constexpr int kImHiBytes = kBlk * kImHiCols * 4;
   static constexpr int kTileA = KT * kBlk;   // raw row tile: KT rows of 128 bytes, 128-byte swizzle
   static constexpr int kTileB = KT * kHalf;  // raw half column tile: KT rows of 64 bytes, 64-byte swizzle
   static constexpr int kRawStage = kTileA + kTileB;
   static constexpr int kPlane = KT * kHalf;  // one decoded B plane (same layout as the raw half)
-  static constexpr int kBStage = 2 * kPlane;
+  static constexpr int kBStage = 3 * kPlane;  // real codes, imaginary codes, negated real codes
   static constexpr int kAcols = KT / 2;      // one A stage: KT / 4 columns of real codes, then imaginary
-  static constexpr int kRowsB = KT / (kDecThreads / 4);  // B rows per decoder thread and stage
+  static constexpr int kRowsB = KT / (kGroupWarps * 32 / 4);  // B rows per decoder thread and stage
   static constexpr int kSteps = KT / 32;                 // MMA steps (32 samples) per stage
   static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kBStage + kStagingBytes + kImHiBytes + kTransposeBytes +
-                               kRowcBytes + kSumsBytes + kScratchBytes + kBarrierBytes;
-  static_assert(KT % 64 == 0, "stages hold whole MMA steps and whole 64-row B passes");
+                               kRowcBytes + kSumsBytes + kScratchBytes + kRscratchBytes + kBarrierBytes;
+  static_assert(KT % 32 == 0, "stages hold whole MMA steps and whole 32-row B passes");
+  // each decoder group waits only on its own raw slots (stage s uses slot s % RAW, decoded by group
+  // s % 2), so no group can test a raw barrier a phase ahead of another group's fill
+  static_assert(RAW % kDecGroups == 0, "raw slots belong to one decoder group each");
   static_assert(kRawStage % 1024 == 0 && kTileA % 1024 == 0, "swizzle atoms stay aligned");
   static_assert(DEC * kAcols <= static_cast<int>(kTmemCols - kAcol0), "A stages fit beside the accumulator");
+  static_assert(STASH >= 0 && STASH <= 8, "stash chunks");
   static_assert((2 * RAW + 2 * DEC + 7) * 8 + 8 + 16 + 16 * kSinkSlots <= kBarrierBytes, "barrier area");
   static_assert(kSmem <= 232448, "shared memory budget");
 };
@@ -201,22 +210,23 @@ __device__ __forceinline__ void prefetch_pair_stage(const CUtensorMap* map_a, co
 // 16-byte chunk swizzle of the Re staging tile (as in the single-SM kernel).
 __device__ __forceinline__ int staging_swizzle(int row) { return ((row & 1) << 2) | ((row >> 1) & 3); }
 
-template <int KT, int RAW, int DEC>
+template <int KT, int RAW, int DEC, int STASH>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     xcorr_tc_fused_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                                const __grid_constant__ PParams p) {
-  using G = PGeom<KT, RAW, DEC>;
+  using G = PGeom<KT, RAW, DEC, STASH>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* raw = smem;                      // [stage][row tile | half column tile]
   uint8_t* bpl = raw + RAW * G::kRawStage;  // [stage][real plane | imaginary plane]
   uint32_t* staging = reinterpret_cast<uint32_t*>(bpl + DEC * G::kBStage);  // Re [row][16-byte chunk ^ swz(row)]
-  uint32_t* im_hi = staging + kBlk * kBlk;                 // Im of columns 64-127, [row][16-byte chunk ^ swz(row)]
-  uint32_t* transpose = im_hi + kImHiBytes / 4;            // [warp][32][kTPitch]
+  uint32_t* im_hi = staging + kBlk * kBlk;                 // Im past the stash, [row][16-byte chunk ^ swz(row)]
+  uint32_t* transpose = im_hi + G::kImHiBytes / 4;         // [warp][32][kTPitch]
   int2* rowc = reinterpret_cast<int2*>(transpose + kEpiWarps * 32 * kTPitch);  // [row]
   int2* sums = rowc + kBlk;
   int2* scratch = sums + 2 * 2 * kBlk;
-  uint64_t* raw_full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(scratch) + kScratchBytes);
+  int2* rscratch = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(scratch) + kScratchBytes);
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(rscratch) + kRscratchBytes);
   uint64_t* raw_empty = raw_full + RAW;
   uint64_t* dec_full = raw_empty + RAW;  // even CTA: both CTAs' decoders filled the stage
   uint64_t* dec_empty = dec_full + DEC;  // both CTAs: the pair's MMAs are done with the stage
@@ -235,12 +245,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < RAW; ++s) {
       mbar_init(&raw_full[s], 1);
-      mbar_init(&raw_empty[s], kDecWarps);
+      mbar_init(&raw_empty[s], kGroupWarps);
     }
     // dec_full, tempty: the even CTA's own warps arrive (one of them expecting the odd CTA's
     // signal bytes); sfull: the local decoders arrive expecting the other CTA's column sums
     for (int s = 0; s < DEC; ++s) {
-      mbar_init(&dec_full[s], kDecWarps);
+      mbar_init(&dec_full[s], kGroupWarps);
       mbar_init(&dec_empty[s], 1);
     }
     mbar_init(tfull, 1);
@@ -306,64 +316,93 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         if (filled & (1u << q)) mbar_wait(&raw_full[q], fill_parity[q], &never, p.status, DEV_TIMEOUT_DRAIN);
     }
   } else if (warp >= kDecWarp0 && warp < kDecWarp0 + kDecWarps) {
+    // Two groups of four decoder warps take alternate stages (group g decodes the CTA's stages
+    // s with s % 2 == g, counted over all its items), so each warp has two stage times for one
+    // stage's decode and its waits, fences and signal.  Warp q of a group (q = warp % 4) owns
+    // tensor-memory lane quarter q (the A codes of inputs 32q .. 32q + 31) and a quarter of the
+    // half column tile's B rows.
     const int dw = warp - kDecWarp0, tid = dw * 32 + lane;
-    // A: this warp's 16 inputs are TMEM lanes 16 ib .. 16 ib + 15, inside its lane quarter warp % 4
-    const int ib = 2 * (warp & 3) + (dw >> 2);
-    const uint32_t a_lanes = static_cast<uint32_t>(16 * ib) << 16;
-    const int arow = lane & 15;                  // ldmatrix row (sample) this thread addresses
-    const int apos = (ib ^ (arow & 7)) << 4;     // chunk ib of that row under the 128-byte swizzle
-    // B: a fixed 16-input chunk L of the half column tile, rows phase, phase + 64, ...; under the
+    const int grp = dw / kGroupWarps, q = warp & 3, gtid = (dw % kGroupWarps) * 32 + lane;
+    const uint32_t a_lanes = static_cast<uint32_t>(32 * q) << 16;
+    const int arow = lane & 15;                    // ldmatrix row (sample) this thread addresses
+    const int apos0 = ((2 * q) ^ (arow & 7)) << 4;  // input chunks 2q, 2q + 1 of that row (128-byte swizzle)
+    const int apos1 = ((2 * q + 1) ^ (arow & 7)) << 4;
+    // B: a fixed 16-input chunk L of the half column tile, rows phase, phase + 32, ...; under the
     // 64-byte swizzle chunk L of row k sits at chunk L ^ ((k >> 1) & 3), the same for every pass
-    const int L = tid & 3, phase = tid >> 2;
+    const int L = gtid & 3, phase = gtid >> 2;
     const int bpos = (L ^ ((phase >> 1) & 3)) << 4;
     const uint32_t dfull_even = smem_cluster(dec_full, 0);  // the even CTA's dec_full[0]
     const uint32_t sink_even = smem_cluster(sink + kSignalBytes * dw, 0);
-    int r = 0, d = 0, g = 0;
-    uint32_t rph = 0, dph = 0;
-    for (int q = cl; q < n_items; q += n_cl, ++g) {
-      const PItem cur = pair_item(p, q, n_items, rank);
-      // A sums: inputs 16 ib + lane / 4 (0) and + 8 (1), over samples 4 (lane % 4) .. + 3 of every 16
-      uint32_t sar0 = 0u, sai0 = 0u, sar1 = 0u, sai1 = 0u;
+    uint32_t gs = 0;  // the CTA's stages before the current item
+    int g = 0;
+    for (int qi = cl; qi < n_items; qi += n_cl, ++g) {
+      const PItem cur = pair_item(p, qi, n_items, rank);
+      // A sums of chunk 2q + c: input 16 (2q + c) + lane / 4 (h = 0) and + 8 (h = 1), over samples
+      // 4 (lane % 4) .. + 3 of every 16
+      uint32_t sar[2][2] = {{0u, 0u}, {0u, 0u}}, sai[2][2] = {{0u, 0u}, {0u, 0u}};
       // B sums in 16-bit lanes: word e / 2, half e % 2 holds input e of chunk L
       uint32_t s_re[8], s_im[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) s_re[k] = s_im[k] = 0u;
       bool ok = true;
-      for (int tb = 0; tb < p.n_kt; ++tb) {
-        if (!mbar_wait_warp(&raw_full[r], rph, abort_flag, p.status, DEV_TIMEOUT_FULL) ||
-            !mbar_wait_warp(&dec_empty[d], dph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
+      for (int tb = (grp ^ static_cast<int>(gs)) & 1; tb < p.n_kt; tb += kDecGroups) {
+        const uint32_t st = gs + static_cast<uint32_t>(tb);  // the CTA's stage index
+        const int r = static_cast<int>(st % RAW), d = static_cast<int>(st % DEC);
+        const uint32_t rph = (st / RAW) & 1u, dph = (st / DEC) & 1u;
+        if (!mbar_wait_warp(&raw_full[r], rph, abort_flag, p.status, DEV_TIMEOUT_FULL)) {
+          ok = false;
+          break;
+        }
+        // the whole raw stage into registers (A: 16 samples x 16 inputs per ldmatrix; B: this
+        // thread's rows), so that the slot goes back to the producer before the decode: its next
+        // fill then overlaps the decode instead of following it
+        constexpr int R = G::kRowsB;
+        const uint8_t* raw_a = raw + r * G::kRawStage;
+        uint32_t xa[KT / 16][2][2];
+        if (cur.has_row) {
+#pragma unroll
+          for (int sb = 0; sb < KT / 16; ++sb)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+              ldmatrix_t_b8(smem_u32(raw_a + (16 * sb + arow) * 128 + (c ? apos1 : apos0)), xa[sb][c][0], xa[sb][c][1]);
+        }
+        uint4 v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+          v[k] = *reinterpret_cast<const uint4*>(raw_a + G::kTileA + bpos + (phase + 32 * k) * kHalf);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&raw_empty[r]);
+        if (!mbar_wait_warp(&dec_empty[d], dph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint8_t* raw_a = raw + r * G::kRawStage;
-        // A operand: 16 samples x 16 inputs per ldmatrix, decoded in registers, stored to TMEM
+        // A operand: decoded in registers, stored to TMEM
         if (cur.has_row) {
-          const uint32_t ta = tmem + a_lanes + kAcol0 + static_cast<uint32_t>(d * G::kAcols);
+          const uint32_t ta = tmem + a_lanes + G::kAcol0 + static_cast<uint32_t>(d * G::kAcols);
 #pragma unroll
           for (int sb = 0; sb < KT / 16; ++sb) {
-            uint32_t x0, x1, re0, im0, re1, im1;
-            ldmatrix_t_b8(smem_u32(raw_a + (16 * sb + arow) * 128 + apos), x0, x1);
-            offset_codes(x0, re0, im0);
-            offset_codes(x1, re1, im1);
-            sar0 = __dp4a(re0, 0x01010101u, sar0);
-            sai0 = __dp4a(im0, 0x01010101u, sai0);
-            sar1 = __dp4a(re1, 0x01010101u, sar1);
-            sai1 = __dp4a(im1, 0x01010101u, sai1);
-            tmem_st_16x128b(ta + 4 * sb, re0, re1);
-            tmem_st_16x128b(ta + KT / 4 + 4 * sb, im0, im1);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              uint32_t re0, im0, re1, im1;
+              offset_codes(xa[sb][c][0], re0, im0);
+              offset_codes(xa[sb][c][1], re1, im1);
+              sar[c][0] = __dp4a(re0, 0x01010101u, sar[c][0]);
+              sai[c][0] = __dp4a(im0, 0x01010101u, sai[c][0]);
+              sar[c][1] = __dp4a(re1, 0x01010101u, sar[c][1]);
+              sai[c][1] = __dp4a(im1, 0x01010101u, sai[c][1]);
+              const uint32_t tc = ta + (static_cast<uint32_t>(16 * c) << 16);
+              tmem_st_16x128b(tc + 4 * sb, re0, re1);
+              tmem_st_16x128b(tc + KT / 4 + 4 * sb, im0, im1);
+            }
           }
         }
         // B operand: this CTA's half of the column tile, real and imaginary planes at the raw
         // chunk's swizzled offset
         {
-          constexpr int R = G::kRowsB;
-          const uint8_t* src = raw_a + G::kTileA + bpos;
           uint8_t* re_t = bpl + d * G::kBStage + bpos;
           uint8_t* im_t = re_t + G::kPlane;
-          uint4 v[R];
-#pragma unroll
-          for (int k = 0; k < R; ++k) v[k] = *reinterpret_cast<const uint4*>(src + (phase + 64 * k) * kHalf);
+          uint8_t* nre_t = im_t + G::kPlane;
           uint32_t a_re[4] = {0u, 0u, 0u, 0u}, a_im[4] = {0u, 0u, 0u, 0u};  // byte lanes: <= 15 R <= 60
 #pragma unroll
           for (int k = 0; k < R; ++k) {
@@ -376,11 +415,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             lane_add(a_re[2], re.z, p.one), lane_add(a_re[3], re.w, p.one);
             lane_add(a_im[0], im.x, p.one), lane_add(a_im[1], im.y, p.one);
             lane_add(a_im[2], im.z, p.one), lane_add(a_im[3], im.w, p.one);
-            const int off = (phase + 64 * k) * kHalf;
+            const int off = (phase + 32 * k) * kHalf;
             *reinterpret_cast<uint4*>(re_t + off) = re;
             *reinterpret_cast<uint4*>(im_t + off) = im;
+            // -u: the E4M3 sign bit (u >= 0)
+            *reinterpret_cast<uint4*>(nre_t + off) =
+                make_uint4(re.x ^ 0x80808080u, re.y ^ 0x80808080u, re.z ^ 0x80808080u, re.w ^ 0x80808080u);
           }
-          // widen to 16-bit lanes: inputs (4q, 4q+1) -> word 2q, (4q+2, 4q+3) -> word 2q+1
+          // widen to 16-bit lanes: inputs (4k, 4k+1) -> word 2k, (4k+2, 4k+3) -> word 2k+1
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             lane_add(s_re[2 * k], __byte_perm(a_re[k], 0u, 0x4140), p.one);
@@ -397,31 +439,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(&raw_empty[r]);
           if (rank != 0)
             bulk_copy_to_cluster(sink_even, token, kSignalBytes, dfull_even + 8u * static_cast<uint32_t>(d));
-          else if (dw == 0)
-            mbar_expect_tx(&dec_full[d], kDecWarps * kSignalBytes);
+          else if (q == 0)
+            mbar_expect_tx(&dec_full[d], kGroupWarps * kSignalBytes);
           else
             mbar_arrive(&dec_full[d]);
         }
-        if (++r == RAW) {
-          r = 0;
-          rph ^= 1u;
-        }
-        if (++d == DEC) {
-          d = 0;
-          dph ^= 1u;
-        }
       }
+      gs += static_cast<uint32_t>(p.n_kt);
       // row sums: the four lanes holding one input's samples are lanes 4k .. 4k + 3
 #pragma unroll
-      for (int m = 1; m <= 2; m <<= 1) {
-        sar0 += __shfl_xor_sync(0xFFFFFFFFu, sar0, m);
-        sai0 += __shfl_xor_sync(0xFFFFFFFFu, sai0, m);
-        sar1 += __shfl_xor_sync(0xFFFFFFFFu, sar1, m);
-        sai1 += __shfl_xor_sync(0xFFFFFFFFu, sai1, m);
-      }
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int m = 1; m <= 2; m <<= 1) {
+            sar[c][h] += __shfl_xor_sync(0xFFFFFFFFu, sar[c][h], m);
+            sai[c][h] += __shfl_xor_sync(0xFFFFFFFFu, sai[c][h], m);
+          }
       // column sums of this warp: lanes L, L + 4, ..., L + 28 hold chunk L
       int2 pq[16];
 #pragma unroll
@@ -442,27 +478,41 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int e = 0; e < 16; ++e) scratch[(dw * 4 + lane) * kPitch + e] = pq[e];
       }
+      // the second group's row sums go through shared memory to the first
+      if (grp == 1 && (lane & 3) == 0) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            rscratch[16 * (2 * q + c) + 8 * h + (lane >> 2)] =
+                make_int2(static_cast<int>(sar[c][h]), static_cast<int>(sai[c][h]));
+      }
       dec_bar_sync(kDecThreads);
       const int buf = g & 1;
       // both CTAs' epilogues must be done with this buffer: the column sums go to both
       if (ok) ok = mbar_wait_warp(&sempty[buf], ((g >> 1) & 1) ^ 1, abort_flag, p.status, DEV_TIMEOUT_TMEM_EMPTY);
       if (ok) {
         int2* rows = sums + (buf * 2) * kBlk;
-        if (cur.has_row && (lane & 3) == 0) {
-          const int e = 16 * ib + (lane >> 2);
-          rows[e] = make_int2(8 * static_cast<int>(sar0 + sai0), 8 * (static_cast<int>(sai0) - static_cast<int>(sar0)));
-          rows[e + 8] =
-              make_int2(8 * static_cast<int>(sar1 + sai1), 8 * (static_cast<int>(sai1) - static_cast<int>(sar1)));
+        if (grp == 0 && cur.has_row && (lane & 3) == 0) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int e = 16 * (2 * q + c) + 8 * h + (lane >> 2);
+              const int2 o = rscratch[e];
+              const int sr = static_cast<int>(sar[c][h]) + o.x, si = static_cast<int>(sai[c][h]) + o.y;
+              rows[e] = make_int2(8 * (sr + si), 8 * (si - sr));
+            }
         }
         if (tid < kHalf) {
-          int2 s = make_int2(0, 0);
+          int2 sm = make_int2(0, 0);
 #pragma unroll
           for (int w = 0; w < kDecWarps; ++w) {
             const int2 x = scratch[(w * 4 + (tid >> 4)) * kPitch + (tid & 15)];
-            s.x += x.x;
-            s.y += x.y;
+            sm.x += x.x;
+            sm.y += x.y;
           }
-          sums[(buf * 2 + 1) * kBlk + kHalf * static_cast<int>(rank) + tid] = make_int2(8 * s.x, 8 * s.y);
+          sums[(buf * 2 + 1) * kBlk + kHalf * static_cast<int>(rank) + tid] = make_int2(8 * sm.x, 8 * sm.y);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // read by the copy below
         }
       }
@@ -477,14 +527,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     }
   } else if (warp == kMmaWarp) {
     if (rank == 0 && lane == 0) {
-      const uint32_t idesc = instr_desc_ta(kTypeE4M3, 256, 128, false);
-      const uint32_t idesc_n = instr_desc_ta(kTypeE4M3, 256, 128, true);
-      constexpr uint32_t kLbo = G::kPlane;  // unused: each CTA's N / 2 = 64 columns are one swizzle atom wide
+      // two M = 256, N = 256 MMAs per 32-sample step; each CTA's 128 B columns are two 64-byte-wide
+      // atoms one plane apart: [re | im] for the real codes of A, [im | -re] for the imaginary ones,
+      // so D holds [Re | Im] of the even CTA's 64 columns, then of the odd CTA's
+      const uint32_t idesc = instr_desc_ta(kTypeE4M3, 256, 256, false);
+      constexpr uint32_t kLbo = G::kPlane;  // between the two atoms of a CTA's 128 columns
       constexpr uint32_t kSbo = 8 * kHalf;  // eight K rows of 64 bytes
       int d = 0, g = 0;
       uint32_t dph = 0;
       bool ok = true;
-      for (int q = cl; ok && q < n_items; q += n_cl, ++g) {
+      for (int qi = cl; ok && qi < n_items; qi += n_cl, ++g) {
         if (!mbar_wait(tempty, (g & 1) ^ 1, abort_flag, p.status, DEV_TIMEOUT_TMEM_EMPTY)) {
           ok = false;
           break;
@@ -496,18 +548,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t a_r = tmem + kAcol0 + static_cast<uint32_t>(d * G::kAcols);
+          const uint32_t a_r = tmem + G::kAcol0 + static_cast<uint32_t>(d * G::kAcols);
           const uint32_t a_i = a_r + KT / 4;
-          const uint32_t b_r = smem_u32(bpl + d * G::kBStage);
-          const uint32_t b_i = b_r + G::kPlane;
+          const uint64_t b_r = smem_desc_sw64(smem_u32(bpl + d * G::kBStage), kLbo, kSbo);
+          const uint64_t b_i = b_r + (G::kPlane >> 4);  // the start address field counts 16 bytes
 #pragma unroll
           for (int k = 0; k < G::kSteps; ++k) {
-            const uint32_t off = static_cast<uint32_t>(k * 32 * kHalf);  // 32 rows of 64 B
-            const uint32_t acc = (tb == 0 && k == 0) ? 0u : 1u;
-            mma_pair_f8f6f4_ta(tmem, a_r + 8 * k, smem_desc_sw64(b_r + off, kLbo, kSbo), idesc, acc);
-            mma_pair_f8f6f4_ta(tmem + 128, a_r + 8 * k, smem_desc_sw64(b_i + off, kLbo, kSbo), idesc, acc);
-            mma_pair_f8f6f4_ta(tmem, a_i + 8 * k, smem_desc_sw64(b_i + off, kLbo, kSbo), idesc, 1u);
-            mma_pair_f8f6f4_ta(tmem + 128, a_i + 8 * k, smem_desc_sw64(b_r + off, kLbo, kSbo), idesc_n, 1u);
+            const uint64_t off = static_cast<uint64_t>((k * 32 * kHalf) >> 4);  // 32 rows of 64 B
+            mma_pair_f8f6f4_ta(tmem, a_r + 8 * k, b_r + off, idesc, (tb == 0 && k == 0) ? 0u : 1u);
+            mma_pair_f8f6f4_ta(tmem, a_i + 8 * k, b_i + off, idesc, 1u);
           }
           mma_pair_commit_both(&dec_empty[d]);
           if (++d == DEC) {
@@ -584,18 +633,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       {
         uint4* srow = reinterpret_cast<uint4*>(staging + r_own * kBlk);
         const int sw = staging_swizzle(r_own);
-        uint4* hrow = reinterpret_cast<uint4*>(im_hi + r_own * (kBlk - 16 * kStashChunks));
+        uint4* hrow = reinterpret_cast<uint4*>(im_hi + r_own * G::kImHiCols);
         for (int ch = 0; ch < n_ch; ++ch) {
+          // D = [Re | Im] of tile columns 0-63, then of 64-127
+          const uint32_t re_col = static_cast<uint32_t>(kChunk * ch + (ch >= kBlk / (2 * kChunk) ? kHalf : 0));
           uint32_t re[16], nim[16];
-          tmem_ld16(taddr + kChunk * ch, re);
-          tmem_ld16(taddr + 128 + kChunk * ch, nim);
+          tmem_ld16(taddr + re_col, re);
+          tmem_ld16(taddr + re_col + kHalf, nim);
           tmem_ld_wait();
-          if (ch < kStashChunks) {
+          if (ch < STASH) {
             tmem_st16(taddr + kStashCol + kChunk * ch, nim);
           } else {
 #pragma unroll
             for (int k = 0; k < kChunk / 4; ++k)
-              hrow[((kChunk * (ch - kStashChunks)) / 4 + k) ^ sw] =
+              hrow[((kChunk * (ch - STASH)) / 4 + k) ^ sw] =
                   make_uint4(nim[4 * k], nim[4 * k + 1], nim[4 * k + 2], nim[4 * k + 3]);
           }
 #pragma unroll
@@ -607,7 +658,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         rowc[r_own] = make_int2(t128 - rs.x - (magic ? kMagicBits : 0), -rs.y + (magic ? kMagicBits : 0));
       }
       // the accumulator (columns 0-255) is free once its loads have landed; the stash stores
-      // (columns 256-319) need only land before phase 2 reads them
+      // (columns 256 .. 256 + 16 STASH - 1) need only land before phase 2 reads them
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
@@ -627,20 +678,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         const int sw = staging_swizzle(r_own);
         for (int ch = 0; ch < n_ch; ++ch) {
           uint32_t im[16];
-          if (ch < kStashChunks) tmem_ld16(taddr + kStashCol + kChunk * ch, im);
+          if (ch < STASH) tmem_ld16(taddr + kStashCol + kChunk * ch, im);
           uint32_t re[16];
 #pragma unroll
           for (int k = 0; k < kChunk / 4; ++k) {
             const uint4 v = *reinterpret_cast<const uint4*>(staging + r_own * kBlk + ((((kChunk * ch) / 4 + k) ^ sw) << 2));
             re[4 * k] = v.x, re[4 * k + 1] = v.y, re[4 * k + 2] = v.z, re[4 * k + 3] = v.w;
           }
-          if (ch < kStashChunks) {
+          if (ch < STASH) {
             tmem_ld_wait();
           } else {
 #pragma unroll
             for (int k = 0; k < kChunk / 4; ++k) {
-              const uint4 v = *reinterpret_cast<const uint4*>(im_hi + r_own * (kBlk - 16 * kStashChunks) +
-                                                              ((((kChunk * (ch - kStashChunks)) / 4 + k) ^ sw) << 2));
+              const uint4 v = *reinterpret_cast<const uint4*>(im_hi + r_own * G::kImHiCols +
+                                                              ((((kChunk * (ch - STASH)) / 4 + k) ^ sw) << 2));
               im[4 * k] = v.x, im[4 * k + 1] = v.y, im[4 * k + 2] = v.z, im[4 * k + 3] = v.w;
             }
           }
@@ -671,7 +722,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         // column sums; 16-byte stores where the row's pairs are 16-byte aligned)
         const int q4 = lane & 3, rg = lane >> 2;
         for (int ch = 0; ch < n_ch; ++ch) {
-          const bool stashed = ch < kStashChunks;  // Im of this chunk in tensor memory (else shared memory)
+          const bool stashed = ch < STASH;  // Im of this chunk in tensor memory (else shared memory)
           const int jl0 = kChunk * ch + 4 * q4;  // this thread's first column in the tile
           const int4 s01 = *reinterpret_cast<const int4*>(cs + jl0);  // (8P, 8Q) of columns jl0, jl0 + 1
           const int4 s23 = *reinterpret_cast<const int4*>(cs + jl0 + 2);
@@ -694,8 +745,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 *reinterpret_cast<const uint4*>(staging + rr * kBlk + (((jl0 >> 2) ^ staging_swizzle(rr)) << 2));
             const uint4 im4 =
                 stashed ? *reinterpret_cast<const uint4*>(tim + rl * kTPitch + 4 * q4)
-                        : *reinterpret_cast<const uint4*>(im_hi + rr * (kBlk - 16 * kStashChunks) +
-                                                          ((((jl0 - 16 * kStashChunks) >> 2) ^ staging_swizzle(rr)) << 2));
+                        : *reinterpret_cast<const uint4*>(im_hi + rr * G::kImHiCols +
+                                                          ((((jl0 - 16 * STASH) >> 2) ^ staging_swizzle(rr)) << 2));
             const int2 rc = rowc[rr];
             const uint32_t vr[4] = {re4.x, re4.y, re4.z, re4.w}, vi[4] = {im4.x, im4.y, im4.z, im4.w};
             const int sp[4] = {s01.x, s01.z, s23.x, s23.z}, sq[4] = {s01.y, s01.w, s23.y, s23.w};
@@ -765,11 +816,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int KT, int RAW, int DEC>
+template <int KT, int RAW, int DEC, int STASH>
 cudaError_t launch_pair(const CUtensorMap& map_a, const CUtensorMap& map_b, const PParams& p, int n_items,
                         int num_sms, cudaStream_t stream) {
-  using G = PGeom<KT, RAW, DEC>;
-  auto kern = xcorr_tc_fused_pair_kernel<KT, RAW, DEC>;
+  using G = PGeom<KT, RAW, DEC, STASH>;
+  auto kern = xcorr_tc_fused_pair_kernel<KT, RAW, DEC, STASH>;
   static int attr_device = -1, max_clusters = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -796,8 +847,9 @@ cudaError_t launch_pair(const CUtensorMap& map_a, const CUtensorMap& map_b, cons
 
 }  // namespace
 
-// The pair shapes: 128 samples with 2 raw + 3 decoded stages, 128 with 3 + 2, 64 with 4 + 6.
-int fused_pair_stage_samples(int variant) { return variant == 2 ? 64 : 128; }
+// The pair shapes: 96 samples with 2 raw + 3 decoded stages (Im of half the tile kept in tensor
+// memory), 128 with 2 + 2 (all of Im in tensor memory), 64 with 4 + 4 (half).
+int fused_pair_stage_samples(int variant) { return variant == 0 ? 96 : variant == 1 ? 128 : 64; }
 
 cudaError_t launch_xcorr_tc_fused_pair_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                            int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
@@ -831,9 +883,9 @@ cudaError_t launch_xcorr_tc_fused_pair_ci4(const uint8_t* in, int row_chans, int
     p.accumulate = (accumulate || t0 > 0) ? 1 : 0;
     cudaError_t e;
     switch (variant) {
-      case 0: e = launch_pair<128, 2, 3>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
-      case 1: e = launch_pair<128, 3, 2>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
-      default: e = launch_pair<64, 4, 6>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
+      case 0: e = launch_pair<96, 2, 3, 4>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
+      case 1: e = launch_pair<128, 2, 2, 8>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
+      default: e = launch_pair<64, 4, 4, 4>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
     }
     if (e != cudaSuccess) return e;
   }
