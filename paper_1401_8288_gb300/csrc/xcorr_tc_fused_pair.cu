@@ -4,40 +4,46 @@
 // Same result as xcorr_tc_fused_ta.cu (per channel, the packed lower triangle
 // of V = sum_t x_t x_t^H; Sec. 1, Sec. 2.1, Eq. 1) from the same raw [t][c][i]
 // CI4 bytes and the same offset-binary E4M3 operands u = t + 8, with the row
-// tile's operand decoded into tensor memory as there.  What limits that kernel
-// is the SM's shared-memory bandwidth: per 128-sample stage the TMA writes of
-// both raw tiles, the decoders' reads and plane writes and the tensor core's
-// reads of B add up to about as many 128-byte wavefronts as the stage has
-// cycles.  Here two CTAs on two SMs work on two tile pairs (c, R0, S) and
-// (c, R1, S) that share the column tile S:
+// tile's operand decoded into tensor memory as there.  Two CTAs of a 2-CTA
+// cluster, on two SMs, work on two tile pairs (c, R0, S) and (c, R1, S) that
+// share the column tile S:
 //
 //   * each CTA decodes its own row tile R into its tensor memory (A) and only
-//     HALF of S, inputs 64 rank .. 64 rank + 63, into its shared memory as two
-//     64-byte-wide planes (real codes, imaginary codes) with the 64-byte swizzle;
-//   * the even CTA issues M = 256, N = 128 MMAs for both: rows 0-127 are the
-//     even CTA's A, rows 128-255 the odd CTA's, and B's columns 0-63 come from
-//     the even CTA's planes, 64-127 from the odd CTA's;
-//   * per 32-sample step:  Re += A_re B_re + A_im B_im,  -Im += A_re B_im - A_im B_re,
-//     four MMAs into the accumulator [Re | -Im] (columns 0-255) of both CTAs,
-//     laid out exactly as in the single-SM kernel.
+//     HALF of S, inputs 64 rank .. 64 rank + 63, into its shared memory as three
+//     64-byte-wide planes with the 64-byte swizzle: real codes, imaginary codes,
+//     negated real codes (the E4M3 sign bit);
+//   * the even CTA issues the MMAs for both, M = 256 (rows 0-127 the even CTA's
+//     A, rows 128-255 the odd CTA's) and N = 256 (columns 0-127 from the even
+//     CTA's planes, 128-255 from the odd CTA's): per 32-sample step
+//     [Re | Im] += A_re [B_re | B_im] and [Re | Im] += A_im [B_im | -B_re], with
+//     Im = A_re B_im - A_im B_re (the accumulated -Im of the correction below),
+//     so the accumulator of each CTA holds [Re | Im] of the even CTA's 64
+//     columns, then of the odd CTA's.  An N = 256 MMA keeps the tensor pipe fed
+//     while decoder warps share the issuing warp's SMSP; a stream of N = 128
+//     MMAs lost 20-40 % there.
 //
 // Per SM and stage this halves the column tile's TMA bytes, decode work and
-// plane writes and the tensor core's operand reads, so the MMAs, not shared
-// memory, bound the kernel.
+// the tensor core's operand reads against the single-SM kernel.
 //
-// A channel's tile pairs are paired by their column tile.  Column tile S has
-// the row tiles S .. nb - 1; where that count is odd, the columns are matched
-// two by two (u, u + 2) and the tile pair (u + 2, u) is computed TRANSPOSED,
-// as rows u against columns u + 2: its epilogue writes V[b][a] = conj(W[a][b]),
-// where each warp holds 32 consecutive a of one output row, so those stores
-// are coalesced as they come out of tensor memory.  Only when the channel has
-// an odd number of tile pairs does one entry keep a single tile pair (the odd
-// CTA's rows are then computed and dropped).
+// A channel's tile pairs are grouped by their column tile (fused_pairing.h).
+// Column tile S has the row tiles S .. nb - 1; where that count is odd, the
+// columns are matched two by two (u, u + 2) and the tile pair (u + 2, u) is
+// computed TRANSPOSED, as rows u against columns u + 2: its epilogue writes
+// V[b][a] = conj(W[a][b]), where each warp holds 32 consecutive a of one output
+// row, so those stores are coalesced as they come out of tensor memory.  Only
+// when the channel has an odd number of tile pairs does one entry keep a single
+// tile pair (the odd CTA's rows are then computed and dropped).
 //
-// The column sums that undo the offset come from the two halves' B decoders
-// and are exchanged through distributed shared memory; the row sums come from
-// each CTA's own A decoders.  Every wait is bounded (sm103_ptx.cuh); the CTAs
-// meet at a cluster barrier before their tensor memory is released.
+// Eight decoder warps form two groups of four (one warp per tensor-memory lane
+// quarter) that take alternate stages; a warp pulls its raw stage into
+// registers and returns the slot to the producer before decoding.  Across the
+// pair, the odd CTA signals the even one with small bulk copies that complete
+// bytes on the even CTA's barriers (a cluster-scope release-arrive stalls the
+// arriving thread for over a thousand cycles), the MMAs' commits multicast to
+// both CTAs, and each CTA's half of the column sums that undo the offset
+// crosses to the other CTA as a bulk copy.  The row sums come from each CTA's
+// own A decoders.  Every wait is bounded (sm103_ptx.cuh); the CTAs meet at a
+// cluster barrier before their tensor memory is released.
 #include "fused_common.cuh"
 #include "fused_pairing.h"
 #include "sm103_ptx.cuh"
