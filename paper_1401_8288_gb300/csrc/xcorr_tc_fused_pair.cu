@@ -799,8 +799,8 @@ cudaError_t launch_pair(const CUtensorMap& map_a, const CUtensorMap& map_b, cons
 }  // namespace
 
 // The pair shapes: 96 samples with 2 raw + 3 decoded stages (Im of half the tile kept in tensor
-// memory), 128 with 2 + 2 (all of Im in tensor memory), 64 with 4 + 4 (half).
-int fused_pair_stage_samples(int variant) { return variant == 0 ? 96 : variant == 1 ? 128 : 64; }
+// memory), 128 with 2 + 2 (all of Im in tensor memory), 96 with 2 + 4 (half).
+int fused_pair_stage_samples(int variant) { return variant == 1 ? 128 : 96; }
 
 cudaError_t launch_xcorr_tc_fused_pair_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                            int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
@@ -836,7 +836,7 @@ cudaError_t launch_xcorr_tc_fused_pair_ci4(const uint8_t* in, int row_chans, int
     switch (variant) {
       case 0: e = launch_pair<96, 2, 3, 4>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
       case 1: e = launch_pair<128, 2, 2, 8>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
-      default: e = launch_pair<64, 4, 4, 4>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
+      default: e = launch_pair<96, 2, 4, 4>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
     }
     if (e != cudaSuccess) return e;
   }
