@@ -146,6 +146,15 @@ __device__ __forceinline__ void tmem_st_16x128b(uint32_t taddr, uint32_t r0, uin
                : "memory");
 }
 
+// As tmem_st_16x128b over eight columns: r0, r1 to columns col .. col + 3, r2, r3
+// to col + 4 .. col + 7.
+__device__ __forceinline__ void tmem_st_16x128b_x2(uint32_t taddr, uint32_t r0, uint32_t r1, uint32_t r2,
+                                                   uint32_t r3) {
+  asm volatile("tcgen05.st.sync.aligned.16x128b.x2.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r0), "r"(r1),
+               "r"(r2), "r"(r3)
+               : "memory");
+}
+
 // 32 lanes x 16 consecutive 32-bit columns, the inverse of tmem_ld16.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
@@ -168,6 +177,15 @@ __device__ __forceinline__ void tmem_st_wait() {
 __device__ __forceinline__ void ldmatrix_t_b8(uint32_t saddr, uint32_t& d0, uint32_t& d1) {
   asm volatile("ldmatrix.sync.aligned.m16n16.x1.trans.shared.b8 {%0, %1}, [%2];"
                : "=r"(d0), "=r"(d1)
+               : "r"(saddr)
+               : "memory");
+}
+// Two such blocks: threads 0-15 give the rows of the first (into d0, d1),
+// threads 16-31 those of the second (into d2, d3).
+__device__ __forceinline__ void ldmatrix_t_b8_x2(uint32_t saddr, uint32_t& d0, uint32_t& d1, uint32_t& d2,
+                                                 uint32_t& d3) {
+  asm volatile("ldmatrix.sync.aligned.m16n16.x2.trans.shared.b8 {%0, %1, %2, %3}, [%4];"
+               : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3)
                : "r"(saddr)
                : "memory");
 }

@@ -275,9 +275,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const int dw = warp - kDecWarp0, tid = dw * 32 + lane;
     const int grp = dw / kGroupWarps, q = warp & 3, gtid = (dw % kGroupWarps) * 32 + lane;
     const uint32_t a_lanes = static_cast<uint32_t>(32 * q) << 16;
-    const int arow = lane & 15;                    // ldmatrix row (sample) this thread addresses
-    const int apos0 = ((2 * q) ^ (arow & 7)) << 4;  // input chunks 2q, 2q + 1 of that row (128-byte swizzle)
-    const int apos1 = ((2 * q + 1) ^ (arow & 7)) << 4;
+    // input chunks 2q, 2q + 1 of row 16 sb + lane (128-byte swizzle; 16 sb = 0 mod 8)
+    const int apos0 = ((2 * q) ^ (lane & 7)) << 4;
+    const int apos1 = ((2 * q + 1) ^ (lane & 7)) << 4;
     // B: a fixed 16-input chunk L of the half column tile, rows phase, phase + 32, ...; under the
     // 64-byte swizzle chunk L of row k sits at chunk L ^ ((k >> 1) & 3), the same for every pass
     const int L = gtid & 3, phase = gtid >> 2;
@@ -309,13 +309,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         // fill then overlaps the decode instead of following it
         constexpr int R = G::kRowsB;
         const uint8_t* raw_a = raw + r * G::kRawStage;
-        uint32_t xa[KT / 16][2][2];
+        uint32_t xa[KT / 16][2][2];  // [16-sample block][input chunk][register]
         if (cur.has_row) {
 #pragma unroll
-          for (int sb = 0; sb < KT / 16; ++sb)
+          for (int sb = 0; sb < KT / 16; sb += 2)
 #pragma unroll
             for (int c = 0; c < 2; ++c)
-              ldmatrix_t_b8(smem_u32(raw_a + (16 * sb + arow) * 128 + (c ? apos1 : apos0)), xa[sb][c][0], xa[sb][c][1]);
+              ldmatrix_t_b8_x2(smem_u32(raw_a + (16 * sb + lane) * 128 + (c ? apos1 : apos0)), xa[sb][c][0],
+                               xa[sb][c][1], xa[sb + 1][c][0], xa[sb + 1][c][1]);
         }
         uint4 v[R];
 #pragma unroll
@@ -332,19 +333,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         if (cur.has_row) {
           const uint32_t ta = tmem + a_lanes + G::kAcol0 + static_cast<uint32_t>(d * G::kAcols);
 #pragma unroll
-          for (int sb = 0; sb < KT / 16; ++sb) {
+          for (int sb = 0; sb < KT / 16; sb += 2) {
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-              uint32_t re0, im0, re1, im1;
+              uint32_t re0, im0, re1, im1, re2, im2, re3, im3;
               offset_codes(xa[sb][c][0], re0, im0);
               offset_codes(xa[sb][c][1], re1, im1);
-              sar[c][0] = __dp4a(re0, 0x01010101u, sar[c][0]);
-              sai[c][0] = __dp4a(im0, 0x01010101u, sai[c][0]);
-              sar[c][1] = __dp4a(re1, 0x01010101u, sar[c][1]);
-              sai[c][1] = __dp4a(im1, 0x01010101u, sai[c][1]);
+              offset_codes(xa[sb + 1][c][0], re2, im2);
+              offset_codes(xa[sb + 1][c][1], re3, im3);
+              // the two blocks' codes of one input add per byte (<= 30) before the dp4a
+              sar[c][0] = __dp4a(re0 + re2, 0x01010101u, sar[c][0]);
+              sai[c][0] = __dp4a(im0 + im2, 0x01010101u, sai[c][0]);
+              sar[c][1] = __dp4a(re1 + re3, 0x01010101u, sar[c][1]);
+              sai[c][1] = __dp4a(im1 + im3, 0x01010101u, sai[c][1]);
               const uint32_t tc = ta + (static_cast<uint32_t>(16 * c) << 16);
-              tmem_st_16x128b(tc + 4 * sb, re0, re1);
-              tmem_st_16x128b(tc + KT / 4 + 4 * sb, im0, im1);
+              tmem_st_16x128b_x2(tc + 4 * sb, re0, re1, re2, re3);
+              tmem_st_16x128b_x2(tc + KT / 4 + 4 * sb, im0, im1, im2, im3);
             }
           }
         }

@@ -261,8 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // A: this warp's 16 inputs are TMEM lanes 16 ib .. 16 ib + 15, inside its lane quarter warp % 4
     const int ib = 2 * (warp & 3) + (dw >> 2);
     const uint32_t a_lanes = static_cast<uint32_t>(16 * ib) << 16;
-    const int arow = lane & 15;                  // ldmatrix row (sample) this thread addresses
-    const int apos = (ib ^ (arow & 7)) << 4;     // chunk ib of that row under the 128-byte swizzle
+    const int apos = (ib ^ (lane & 7)) << 4;     // chunk ib of row 16 sb + lane under the 128-byte swizzle
     // B: a fixed 16-input chunk L of the column tile, rows phase, phase + 32, ...
     const int L = tid & 7, phase = tid >> 3;
     const int bpos = (L ^ (phase & 7)) << 4;
@@ -286,20 +285,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint8_t* raw_a = raw + r * G::kRawStage;
         const uint8_t* raw_b = raw_a + (cur.diag ? 0 : G::kTile);
-        // A operand: 16 samples x 16 inputs per ldmatrix, decoded in registers, stored to TMEM
+        // A operand: two blocks of 16 samples x 16 inputs per ldmatrix (thread t addresses row
+        // 16 sb + t, both blocks under the same swizzle since 16 sb = 0 mod 8), decoded in
+        // registers, stored to TMEM eight columns at a time
         const uint32_t ta = tmem + a_lanes + kAcol0 + static_cast<uint32_t>(d * G::kAcols);
+        static_assert(KT % 32 == 0, "whole pairs of 16-sample blocks");
 #pragma unroll
-        for (int sb = 0; sb < KT / 16; ++sb) {
-          uint32_t x0, x1, re0, im0, re1, im1;
-          ldmatrix_t_b8(smem_u32(raw_a + (16 * sb + arow) * 128 + apos), x0, x1);
+        for (int sb = 0; sb < KT / 16; sb += 2) {
+          uint32_t x0, x1, x2, x3, re0, im0, re1, im1, re2, im2, re3, im3;
+          ldmatrix_t_b8_x2(smem_u32(raw_a + (16 * sb + lane) * 128 + apos), x0, x1, x2, x3);
           offset_codes(x0, re0, im0);
           offset_codes(x1, re1, im1);
-          sar0 = __dp4a(re0, 0x01010101u, sar0);
-          sai0 = __dp4a(im0, 0x01010101u, sai0);
-          sar1 = __dp4a(re1, 0x01010101u, sar1);
-          sai1 = __dp4a(im1, 0x01010101u, sai1);
-          tmem_st_16x128b(ta + 4 * sb, re0, re1);
-          tmem_st_16x128b(ta + KT / 4 + 4 * sb, im0, im1);
+          offset_codes(x2, re2, im2);
+          offset_codes(x3, re3, im3);
+          // the two blocks' codes of one input add per byte (<= 30) before the dp4a
+          sar0 = __dp4a(re0 + re2, 0x01010101u, sar0);
+          sai0 = __dp4a(im0 + im2, 0x01010101u, sai0);
+          sar1 = __dp4a(re1 + re3, 0x01010101u, sar1);
+          sai1 = __dp4a(im1 + im3, 0x01010101u, sai1);
+          tmem_st_16x128b_x2(ta + 4 * sb, re0, re1, re2, re3);
+          tmem_st_16x128b_x2(ta + KT / 4 + 4 * sb, im0, im1, im2, im3);
         }
         // B operand: real and imaginary planes in shared memory at the raw chunk's swizzled offset
         {
