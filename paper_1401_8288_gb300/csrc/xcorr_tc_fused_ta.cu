@@ -9,12 +9,12 @@
 // decoders' stores and the TMA writes together exhaust the SM's shared-memory
 // bandwidth well before the tensor pipe; here A lives in tensor memory:
 //
-//   * one ldmatrix.trans of a 16-sample x 16-input block of raw bytes gives
+//   * an ldmatrix.trans of a 16-sample x 16-input block of raw bytes gives
 //     each thread four consecutive samples of one input, which is exactly the
 //     register layout a tcgen05.st of 16 lanes x 128 bits takes (lane = input,
 //     column = four samples); after the XOR-and-mask decode the registers go
 //     to tensor memory unchanged, one store for the real codes and one for the
-//     imaginary codes;
+//     imaginary codes (the .x2 forms of both move two such blocks at once);
 //   * the column tile's real and imaginary planes are decoded into shared
 //     memory as before (MN-major, 128-byte swizzle) and are the MMAs' B;
 //   * per 32-sample step the MMAs are Re|-Im += A_re [B_re | B_im],
