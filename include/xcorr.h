@@ -23,13 +23,30 @@
  *                  per component; the nibble order is this library's
  *                  reading, the paper does not fix it).
  *   XCORR_IN_CI8   int8 pair (re, im), the unpacked 8-bit form of Sec. 2.4.
- *   XCORR_IN_CF32  float pair (re, im), spectra from a GPU F-stage (Sec. 1);
- *                  finite values, magnitudes in [2^-60, 2^60].  Each input's
- *                  samples are quantised per 384-sample window against the
- *                  window's largest magnitude (23 bits) and split into three
- *                  integer digits; the six leading digit products are summed
- *                  exactly per window and scaled into a float accumulator.
- *                  The error is about 1e-7 of sqrt(|V_ii V_jj|) per entry.
+ *   XCORR_IN_CF32  float pair (re, im), spectra from a GPU F-stage (Sec. 1).
+ *                  Each input's samples are quantised per 384-sample window
+ *                  against the window's largest magnitude (23 bits) and split
+ *                  into three integer digits; the six leading digit products
+ *                  are summed exactly per window and scaled into a float
+ *                  accumulator.  The error is about 1e-7 of
+ *                  sqrt(|V_ii V_jj|) per entry (at most 1e-6).
+ *                  Edge values, all handled without flushing:
+ *                  - subnormal samples, and whole windows of them, are
+ *                    quantised on a grid of 2^-149 or finer, which holds
+ *                    every float exactly, so any finite input keeps the
+ *                    bound above (there is no lower magnitude limit);
+ *                  - results are float: an entry whose exact value lies below
+ *                    the normal float range (2^-126) comes out as a float
+ *                    subnormal or zero; one whose partial sums pass the
+ *                    float range (about 3.4e38) comes out non-finite (+-inf,
+ *                    or NaN where partial sums of both signs overflow);
+ *                  - a NaN or +-inf sample makes every entry that pairs its
+ *                    input with any input (its own autocorrelation
+ *                    included) NaN, re and im, in that channel, for the rest
+ *                    of the integration and in every dump that holds it; all
+ *                    other entries are unaffected.  Where the exact sum has
+ *                    a non-finite term, so does this result (NaN where the
+ *                    FP64 sum has an inf or a NaN).
  *
  * Output layout: the packed lower triangle per channel, pair index
  * p(i, j) = i (i + 1) / 2 + j for i >= j, (re, im) interleaved:
@@ -140,11 +157,13 @@ xcorr_status xcorr_plan_create(xcorr_plan *out, const xcorr_config *cfg);
  * Correlate n_time samples and add them to the running integration
  * (Sec. 2.1: cross multiplication and integration per channel and sample).
  * d_in: caller-owned DEVICE memory, [n_time][n_channels][n_stations][2]
- * samples in the plan's format (any alignment; 16-byte alignment and N_i a
- * multiple of 16 take the vectorised paths), read-only; it must stay
- * valid until the stream passes this call.  1 <= n_time <= max_time_per_exec.
+ * samples in the plan's format (CI4 and CI8 at any alignment, CF32 4-byte
+ * aligned; 16-byte alignment and N_i a multiple of 16 take the vectorised
+ * paths), read-only; it must stay valid until the stream passes this call.
+ * 1 <= n_time <= max_time_per_exec.
  * stream: a cudaStream_t (NULL = the legacy default stream).
- * Errors: INVALID_ARG, OVERFLOW (samples since reset + n_time would exceed
+ * Errors: INVALID_ARG (also a CF32 pointer that is not 4-byte aligned),
+ * OVERFLOW (samples since reset + n_time would exceed
  * max_integration; nothing is launched), DEVICE, CUDA.
  */
 xcorr_status xcorr_execute(xcorr_plan plan, const void *d_in, int n_time, void *stream);
@@ -279,13 +298,20 @@ xcorr_status xcorr_measure_peak(int kind, double *tops);
  * alignment), d_out receives int32 [n_channels][P][2] (device memory, written,
  * not added to).  d_status, if not NULL, is a device int that receives the
  * kernels' status word (0 = success).  Both buffers are the caller's.
+ * d_status is the only way to learn that a kernel's bounded wait ran out
+ * (the call has already returned XCORR_OK by then, and d_out is then only
+ * partly written): callers should pass it and check it after the stream
+ * passes the call.
  *
  * The staging planes live in a fixed 64 MiB array that every GPU loading the
  * library holds until the process exits; a call needs
  * 2 * n_channels * n_time * round_up(2 * n_stations, 16) bytes of it and is
- * refused with INVALID_ARG beyond 64 MiB - 256 bytes.  The first call on a
- * device looks up the array's device address (make that first call before
- * any stream capture).  Every call uses the same array and leaves its
+ * refused with INVALID_ARG beyond 64 MiB - 256 bytes.  The array's device
+ * address is looked up on every call whose stream is not being captured, so
+ * it follows a cudaDeviceReset or a change of CUDA context; a call on a
+ * capturing stream reuses the address last seen for that device and context,
+ * so the first call on a device (and after a reset or in a new context) must
+ * come before any stream capture.  Every call uses the same array and leaves its
  * contents behind, so calls whose work overlaps on the GPU (different
  * streams, or different host threads) race and must be serialised by the
  * caller.  The call returns without waiting for the GPU.

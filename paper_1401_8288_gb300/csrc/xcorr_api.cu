@@ -85,6 +85,8 @@ xcorr_status check_execute(xcorr_plan plan, const void* d_in, int n_time) {
   xcorr_status st = plan_ok(plan);
   if (st != XCORR_OK) return st;
   if (!d_in) return fail(XCORR_ERR_INVALID_ARG, "d_in is NULL");
+  if (plan->cfg.fmt == XCORR_IN_CF32 && reinterpret_cast<uintptr_t>(d_in) % 4)
+    return fail(XCORR_ERR_INVALID_ARG, "float input must be 4-byte aligned");
   if (n_time < 1 || n_time > plan->cfg.max_time_per_exec)
     return fail(XCORR_ERR_INVALID_ARG, "n_time must be in [1, max_time_per_exec]");
   if (plan->samples + n_time > plan->max_integration)
@@ -312,7 +314,7 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
                                                             : 0;
   const int exp_windows = (c.max_time_per_exec + xc::kTcWindowBF16 - 1) / xc::kTcWindowBF16;
   const size_t exps_bytes =
-      (engine == XCORR_ENGINE_TENSOR && c.fmt == XCORR_IN_CF32) ? (size_t)c.n_channels * exp_windows * ni_pad : 0;
+      (engine == XCORR_ENGINE_TENSOR && c.fmt == XCORR_IN_CF32) ? (size_t)c.n_channels * exp_windows * ni_pad * 2 : 0;
   const size_t dev_bytes = acc_bytes + planes_bytes + exps_bytes + 256;
   if (c.hbm_budget_bytes && dev_bytes > c.hbm_budget_bytes)
     return fail(XCORR_ERR_BUDGET, "plan needs " + std::to_string(dev_bytes) + " device bytes, budget is " +

@@ -36,6 +36,24 @@ constexpr int kDefaultFusedVariant = 4;  // 4-bit plans before any tuning: A in 
 // The planes path's shape for a tuning's stage_variant (3 exists only for the fused kernel).
 inline int planes_variant(int v) { return v >= kTcVariants ? 1 : v; }
 constexpr int64_t kMaxIntegrationCF32 = INT64_C(16777216);  // FP32 per dump, widen beyond
+// Float input: window exponents E = floor(log2(largest magnitude of the window)), so every
+// component is below 2^(E+1), lie in [kExpMin, 127] (int16); a window of zeros takes kExpMin.
+// A subnormal maximum gets its own exponent too, so the window's 23-bit quantisation keeps its
+// full length (a subnormal m 2^-149 is the integer m 2^(-127 - E) on that window's grid).  A
+// window holding a NaN or an infinity is marked kExpNonFinite, and every block that involves
+// it drains as NaN.
+constexpr int kExpMin = -149;
+constexpr int kExpNonFinite = -256;
+
+// 2^n as a float for -149 <= n <= 127 (subnormal below -126), built from its bits.
+__host__ __device__ __forceinline__ float pow2i(int n) {
+  union {
+    uint32_t u;
+    float f;
+  } v;
+  v.u = n >= -126 ? static_cast<uint32_t>(n + 127) << 23 : 1u << (n + 149);
+  return v.f;
+}
 
 enum ExecMode : int { MODE_STORE = 0, MODE_ADD = 1, MODE_ATOMIC = 2 };
 
@@ -62,7 +80,7 @@ struct xcorr_plan_s {
 
   void* acc = nullptr;         // [C][P] (re, im): int32 (integer input) or float (float input)
   void* planes = nullptr;      // tensor path: [C][planes_per_chan][max_time][ni_pad] numbers
-  int8_t* exps = nullptr;      // float input: window exponents [C][exp_windows][ni_pad]
+  int16_t* exps = nullptr;     // float input: window exponents [C][exp_windows][ni_pad]
   int exp_windows = 0;
   size_t planes_bytes = 0;
   int elem_bytes = 1;          // plane numbers: 1 = E4M3, 2 = BF16
@@ -129,7 +147,7 @@ struct TcLaunch {
   int n_pairs_k = 1;        // plane pairs on the virtual K axis
   int pair_p[8] = {0}, pair_q[8] = {0};
   int window_samples = kTcWindowCI4;  // samples per drained block
-  const int8_t* exps = nullptr;       // float input: window exponents [C][exp_windows][ni_pad]
+  const int16_t* exps = nullptr;      // float input: window exponents [C][exp_windows][ni_pad]
   int exp_windows = 0, ni_pad = 0;
   bool accumulate = false;  // add into out (else the first block stores)
   void* out = nullptr;      // int2 or float2 [C][P]
@@ -224,7 +242,7 @@ cudaError_t launch_unpack_ci8_bf16(const int8_t* in, uint16_t* planes, int n_tim
                                    cudaStream_t stream);
 // float (re, im) samples -> six BF16 planes [c][6][t][ni_pad] of integer digits
 // (re digits 0-2, im digits 0-2) and one exponent per (channel, window, input).
-cudaError_t launch_unpack_cf32_digits(const float* in, uint16_t* planes, int8_t* exps, int n_time, int n_chan,
+cudaError_t launch_unpack_cf32_digits(const float* in, uint16_t* planes, int16_t* exps, int n_time, int n_chan,
                                       int c0, int nc, int n_inputs, int ni_pad, int max_time, int window,
                                       int exp_windows, cudaStream_t stream);
 cudaError_t launch_fold_wide_f64(const float2* acc, double* out, int64_t n_pairs_total, cudaStream_t stream);

@@ -25,26 +25,66 @@ constexpr size_t kStatusBytes = 256;               // kernel status word, then t
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the first call on a device does this).
-xcorr_status scratch_address(void** out) {
+// The array's device address belongs to the module as loaded in one CUDA context: after a
+// cudaDeviceReset, or in a caller's own driver-API context, the module is loaded again and the
+// array sits elsewhere.  So the address is cached per device together with the context it was
+// looked up in, and looked up again on every call whose stream is not being captured (a cheap
+// runtime call); a stream under capture reuses the address cached for this device and context.
+struct ScratchEntry {
+  CUcontext ctx = nullptr;
+  void* addr = nullptr;
+};
+std::mutex g_scratch_mu;
+ScratchEntry g_scratch[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+xcorr_status current_context(CUcontext* out) {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  });
+  if (!fn) return xc::set_error(XCORR_ERR_CUDA, "cuCtxGetCurrent is not available from the driver");
+  if (fn(out) != CUDA_SUCCESS) return xc::set_error(XCORR_ERR_CUDA, "cuCtxGetCurrent failed");
+  return XCORR_OK;
+}
+
+// Device address of the scratch array for the current device and context.
+xcorr_status scratch_address(cudaStream_t stream, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return xc::set_error(XCORR_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return xc::set_error(XCORR_ERR_UNSUPPORTED, "device ordinal above 63");
+  CUcontext ctx = nullptr;
+  xcorr_status st = current_context(&ctx);
+  if (st != XCORR_OK) return st;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+    cudaGetLastError();  // the query itself is refused while another stream captures: keep the cache
+    cs = cudaStreamCaptureStatusActive;
+  }
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  ScratchEntry& en = g_scratch[dev];
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return xc::set_error(XCORR_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") +
                                                cudaGetErrorString(e));
-    g_scratch_addr[dev] = p;
+    en.ctx = ctx;
+    en.addr = p;
+  } else if (!en.addr || en.ctx != ctx) {
+    return xc::set_error(XCORR_ERR_INVALID_ARG,
+                         "the stream is being captured and this device and context have no scratch address yet: "
+                         "make one call outside the capture first");
   }
-  *out = g_scratch_addr[dev];
+  *out = en.addr;
   return XCORR_OK;
 }
 
@@ -58,10 +98,12 @@ extern "C" xcorr_status xcorr_correlate_ci4_noalloc(const void* d_in, int n_time
     return xc::set_error(XCORR_ERR_INVALID_ARG, "n_time, n_channels and n_stations must be >= 1");
   if (n_time > xc::kMaxIntegrationCI4)
     return xc::set_error(XCORR_ERR_OVERFLOW, "n_time exceeds the exact int32 bound of 16,777,215 samples");
+  if (n_stations > (1 << 20))
+    return xc::set_error(XCORR_ERR_INVALID_ARG, "n_stations must be at most 2^20");
   const int n_inputs = 2 * n_stations;
   const int ni_pad = (n_inputs + 15) / 16 * 16;
   const size_t planes = size_t(2) * size_t(n_channels) * size_t(n_time) * size_t(ni_pad);
-  if (n_stations > (1 << 20) || planes > kScratchBytes - kStatusBytes)
+  if (planes > kScratchBytes - kStatusBytes)
     return xc::set_error(XCORR_ERR_INVALID_ARG,
                          "this correlation needs " + std::to_string(planes) +
                              " bytes of staging planes (2 * n_channels * n_time * N_i rounded up to 16); "
@@ -75,12 +117,12 @@ extern "C" xcorr_status xcorr_correlate_ci4_noalloc(const void* d_in, int n_time
   if (e != cudaSuccess) return xc::set_error(XCORR_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
   if (major != 10 || minor != 3) return xc::set_error(XCORR_ERR_UNSUPPORTED, "needs an sm_103a (GB300) device");
 
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* scratch = nullptr;
-  xcorr_status st = scratch_address(&scratch);
+  xcorr_status st = scratch_address(s, &scratch);
   if (st != XCORR_OK) return st;
   int* status = static_cast<int*>(scratch);
   uint8_t* plane_buf = static_cast<uint8_t*>(scratch) + kStatusBytes;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   // The array keeps the previous call's contents: the status word must start at zero.
   // (The planes need no clearing: the unpack writes every element the X kernel reads.)

@@ -95,7 +95,7 @@ struct TcParams {
   int accumulate_first;  // the first block adds into out (else it stores)
   void* out;             // int2 or float2 [C][P]
   int* status;
-  const int8_t* exps;    // float input: window exponents [C][exp_windows][ni_pad]
+  const int16_t* exps;   // float input: window exponents [C][exp_windows][ni_pad]
   int exp_windows, ni_pad;
   int8_t pair_p[8], pair_q[8];  // digit indices of each plane pair
   // batch mode: items (subarray, channel, I, J), longest first
@@ -337,21 +337,27 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        // float input: this block's scale 2^(E_i + E_j - 12 - 8(p + q))
-        const int8_t* exps_w = nullptr;
-        float row_scale = 1.f;
+        // float input: this block's scale 2^k, k = E_i + E_j - 12 - 8(p + q); the row's part here
+        const int16_t* exps_w = nullptr;
+        int row_k = 0;
+        bool row_bad = false;
         if (FLOAT_OUT) {
           const int w = blk / p.n_pairs_k, pk = blk - w * p.n_pairs_k;
           exps_w = p.exps + ((int64_t)v.chan * p.exp_windows + w) * p.ni_pad;
           const int i_row = min(row0 + lane, n_inputs - 1);
-          row_scale = ldexpf(1.f, static_cast<int>(exps_w[i_row]) - 12 - 8 * (p.pair_p[pk] + p.pair_q[pk]));
+          const int e_row = exps_w[i_row];
+          row_k = e_row - 12 - 8 * (p.pair_p[pk] + p.pair_q[pk]);
+          row_bad = e_row == kExpNonFinite;
         }
         const uint32_t taddr =
             tmem + (static_cast<uint32_t>(quarter * 32) << 16) + buf * kAccCols + colh * kCols;
         if (FLOAT_OUT) {
-          // exact integer block sums times an exact power of two; the column
-          // exponents of 8 columns come in one 8-byte load (padding entries
-          // are zero)
+          // exact integer block sums times an exact power of two 2^k, applied as two factors
+          // 2^(k >> 1) and 2^(k - (k >> 1)) so that neither leaves the float range
+          // (k <= 242): a sum whose product overflows becomes +-inf, a zero sum stays zero, and
+          // a product below the normal range rounds once, as a subnormal.  A window with a
+          // non-finite sample makes its blocks NaN.  The column exponents of 8 columns come in
+          // one 16-byte load (padding entries are zero).
 #pragma unroll
           for (int k = 0; k < kCols / 8; ++k) {
             uint32_t re[8], nim[8];
@@ -359,13 +365,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_ld8(taddr + 128 + 8 * k, nim);
             tmem_ld_wait();
             if (live) {
-              const uint2 e8 = *reinterpret_cast<const uint2*>(exps_w + col0 + 8 * k);
+              const uint4 e8 = *reinterpret_cast<const uint4*>(exps_w + col0 + 8 * k);
+              const uint32_t ew[4] = {e8.x, e8.y, e8.z, e8.w};
 #pragma unroll
               for (int q = 0; q < 8; ++q) {
-                const int ej = static_cast<int8_t>(((q < 4 ? e8.x : e8.y) >> (8 * (q & 3))) & 0xFF);
-                const float sc = ldexpf(row_scale, ej);
-                acc_re[8 * k + q] += __uint_as_float(re[q]) * sc;
-                acc_im[8 * k + q] -= __uint_as_float(nim[q]) * sc;
+                const int ej = static_cast<int16_t>((ew[q >> 1] >> (16 * (q & 1))) & 0xFFFFu);
+                // below -298 a block's contribution rounds to zero either way
+                const int kk = max(row_k + ej, -298);
+                const float f1 = (row_bad || ej == kExpNonFinite) ? __int_as_float(0x7FC00000) : pow2i(kk >> 1);
+                const float f2 = pow2i(kk - (kk >> 1));
+                acc_re[8 * k + q] += (__uint_as_float(re[q]) * f1) * f2;
+                acc_im[8 * k + q] -= (__uint_as_float(nim[q]) * f1) * f2;
               }
             }
           }

@@ -231,8 +231,39 @@ __global__ void __launch_bounds__(256) unpack_ci8_bf16_elem(const int8_t* __rest
 // M = rint(x 2^(22-E)) (|M| < 2^23, error <= 2^-23 max), and write the
 // balanced base-256 digits of M = d0 2^16 + d1 2^8 + d2 (|d_p| <= 128, exact
 // BF16 values) to planes re_p = p and im_p = 3 + p.  E goes to exps.
-__device__ __forceinline__ void digits_of(float x, float scale, uint16_t (&d)[3]) {
-  const int m = __float2int_rn(x * scale);
+//
+// Edges.  The maximum is taken over the components' bit patterns with the
+// sign cleared: for non-negative floats they order as the values do, and the
+// patterns of infinities and NaNs lie above every finite one, so one integer
+// maximum also finds a non-finite sample.  Such a window gets E =
+// kExpNonFinite and zero digits; the X kernel's drain turns every block that
+// involves it into NaN.  A window whose maximum is subnormal gets that
+// maximum's own exponent (down to -149), so its samples keep 23-bit integers
+// like any other window's and no finite input is flushed.  2^(22-E) spans
+// 2^-105 .. 2^171, past the float range, so it is applied as two exact
+// power-of-two factors.
+__device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
+
+__device__ __forceinline__ int window_exponent(uint32_t max_bits) {
+  if (max_bits >= 0x7F800000u) return kExpNonFinite;
+  if (max_bits >= 0x00800000u) return static_cast<int>(max_bits >> 23) - 127;  // normal
+  if (max_bits == 0u) return kExpMin;
+  return (31 - __clz(static_cast<int>(max_bits))) - 149;  // subnormal m 2^-149: floor(log2 m) - 149
+}
+
+// The two factors of 2^(22 - e), each in [2^-53, 2^86]; zero for a non-finite window.
+__device__ __forceinline__ void window_scale(int e, float& s1, float& s2) {
+  if (e == kExpNonFinite) {
+    s1 = s2 = 0.f;
+    return;
+  }
+  const int n = 22 - e, a = n >> 1;
+  s1 = pow2i(a);
+  s2 = pow2i(n - a);
+}
+
+__device__ __forceinline__ void digits_of(float x, float s1, float s2, uint16_t (&d)[3]) {
+  const int m = __float2int_rn((x * s1) * s2);
   const int d2 = ((m + 128) & 255) - 128;
   const int m1 = (m - d2) >> 8;
   const int d1 = ((m1 + 128) & 255) - 128;
@@ -242,9 +273,10 @@ __device__ __forceinline__ void digits_of(float x, float scale, uint16_t (&d)[3]
   d[2] = __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d2)));
 }
 
-__global__ void __launch_bounds__(256) unpack_cf32_digits_kernel(const float2* __restrict__ in,
+// Any 4-byte aligned input: the components are read as single floats.
+__global__ void __launch_bounds__(256) unpack_cf32_digits_kernel(const float* __restrict__ in,
                                                                  uint16_t* __restrict__ planes,
-                                                                 int8_t* __restrict__ exps, int n_time, int n_chan,
+                                                                 int16_t* __restrict__ exps, int n_time, int n_chan,
                                                                  int c0, int nc, int n_inputs, int ni_pad,
                                                                  int64_t comp_stride, int window, int exp_windows) {
   const int n_w = (n_time + window - 1) / window;
@@ -256,27 +288,23 @@ __global__ void __launch_bounds__(256) unpack_cf32_digits_kernel(const float2* _
     const int w = static_cast<int>(rest % n_w);
     const int c = c0 + static_cast<int>(rest / n_w);
     const int t0 = w * window, t1 = min(n_time, t0 + window);
-    float mx = 0.f;
+    uint32_t mb = 0u;
 #pragma unroll 8
     for (int t = t0; t < t1; ++t) {
-      const float2 v = __ldg(in + ((int64_t)t * n_chan + c) * n_inputs + i);
-      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+      const float* v = in + 2 * (((int64_t)t * n_chan + c) * n_inputs + i);
+      mb = max(mb, max(abs_bits(__ldg(v)), abs_bits(__ldg(v + 1))));
     }
-    int e = 0;
-    if (mx > 0.f) {
-      frexpf(mx, &e);  // mx = f 2^e with f in [0.5, 1): mx < 2^e
-      e -= 1;
-    }
-    e = max(e, -64);
-    exps[((int64_t)c * exp_windows + w) * ni_pad + i] = static_cast<int8_t>(e);
-    const float scale = ldexpf(1.f, 22 - e);
+    const int e = window_exponent(mb);
+    exps[((int64_t)c * exp_windows + w) * ni_pad + i] = static_cast<int16_t>(e);
+    float s1, s2;
+    window_scale(e, s1, s2);
     uint16_t* base = planes + (6 * (int64_t)c) * comp_stride + i;
 #pragma unroll 4
     for (int t = t0; t < t1; ++t) {
-      const float2 v = __ldg(in + ((int64_t)t * n_chan + c) * n_inputs + i);
+      const float* v = in + 2 * (((int64_t)t * n_chan + c) * n_inputs + i);
       uint16_t dr[3], dm[3];
-      digits_of(v.x, scale, dr);
-      digits_of(v.y, scale, dm);
+      digits_of(__ldg(v), s1, s2, dr);
+      digits_of(__ldg(v + 1), s1, s2, dm);
       uint16_t* row = base + (int64_t)t * ni_pad;
 #pragma unroll
       for (int pc = 0; pc < 3; ++pc) {
@@ -292,7 +320,7 @@ __global__ void __launch_bounds__(256) unpack_cf32_digits_kernel(const float2* _
 // 4-byte stores of two digits, half the instructions per byte.
 __global__ void __launch_bounds__(256) unpack_cf32_digits_x2_kernel(const float4* __restrict__ in,
                                                                     uint16_t* __restrict__ planes,
-                                                                    int8_t* __restrict__ exps, int n_time,
+                                                                    int16_t* __restrict__ exps, int n_time,
                                                                     int n_chan, int c0, int nc, int n_inputs,
                                                                     int ni_pad, int64_t comp_stride, int window,
                                                                     int exp_windows) {
@@ -308,38 +336,30 @@ __global__ void __launch_bounds__(256) unpack_cf32_digits_x2_kernel(const float4
     const int t0 = w * window, t1 = min(n_time, t0 + window);
     const float4* col = in + (int64_t)c * half + i2;  // inputs 2 i2, 2 i2 + 1 of channel c, time 0
     const int64_t row_step = (int64_t)n_chan * half;  // float4s from one sample to the next
-    float mx0 = 0.f, mx1 = 0.f;
+    uint32_t mb0 = 0u, mb1 = 0u;
 #pragma unroll 8
     for (int t = t0; t < t1; ++t) {
       const float4 v = __ldg(col + t * row_step);
-      mx0 = fmaxf(mx0, fmaxf(fabsf(v.x), fabsf(v.y)));
-      mx1 = fmaxf(mx1, fmaxf(fabsf(v.z), fabsf(v.w)));
+      mb0 = max(mb0, max(abs_bits(v.x), abs_bits(v.y)));
+      mb1 = max(mb1, max(abs_bits(v.z), abs_bits(v.w)));
     }
-    int e0 = 0, e1 = 0;
-    if (mx0 > 0.f) {
-      frexpf(mx0, &e0);
-      e0 -= 1;
-    }
-    if (mx1 > 0.f) {
-      frexpf(mx1, &e1);
-      e1 -= 1;
-    }
-    e0 = max(e0, -64);
-    e1 = max(e1, -64);
-    int8_t* ex = exps + ((int64_t)c * exp_windows + w) * ni_pad + 2 * i2;
-    ex[0] = static_cast<int8_t>(e0);
-    ex[1] = static_cast<int8_t>(e1);
-    const float s0 = ldexpf(1.f, 22 - e0), s1 = ldexpf(1.f, 22 - e1);
+    const int e0 = window_exponent(mb0), e1 = window_exponent(mb1);
+    int16_t* ex = exps + ((int64_t)c * exp_windows + w) * ni_pad + 2 * i2;
+    ex[0] = static_cast<int16_t>(e0);
+    ex[1] = static_cast<int16_t>(e1);
+    float s0a, s0b, s1a, s1b;
+    window_scale(e0, s0a, s0b);
+    window_scale(e1, s1a, s1b);
     uint32_t* base = reinterpret_cast<uint32_t*>(planes + (6 * (int64_t)c) * comp_stride + 2 * i2);
     const int64_t cs = comp_stride / 2;  // in uint32 units (comp_stride is a multiple of 16)
 #pragma unroll 4
     for (int t = t0; t < t1; ++t) {
       const float4 v = __ldg(col + t * row_step);
       uint16_t r0[3], m0[3], r1[3], m1[3];
-      digits_of(v.x, s0, r0);
-      digits_of(v.y, s0, m0);
-      digits_of(v.z, s1, r1);
-      digits_of(v.w, s1, m1);
+      digits_of(v.x, s0a, s0b, r0);
+      digits_of(v.y, s0a, s0b, m0);
+      digits_of(v.z, s1a, s1b, r1);
+      digits_of(v.w, s1a, s1b, m1);
       uint32_t* row = base + (int64_t)t * (ni_pad / 2);
 #pragma unroll
       for (int pc = 0; pc < 3; ++pc) {
@@ -377,7 +397,7 @@ cudaError_t launch_unpack_ci8_bf16(const int8_t* in, uint16_t* planes, int n_tim
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack_cf32_digits(const float* in, uint16_t* planes, int8_t* exps, int n_time, int n_chan,
+cudaError_t launch_unpack_cf32_digits(const float* in, uint16_t* planes, int16_t* exps, int n_time, int n_chan,
                                       int c0, int nc, int n_inputs, int ni_pad, int max_time, int window,
                                       int exp_windows, cudaStream_t stream) {
   const int64_t comp_stride = (int64_t)max_time * ni_pad;
@@ -391,7 +411,7 @@ cudaError_t launch_unpack_cf32_digits(const float* in, uint16_t* planes, int8_t*
         reinterpret_cast<const float4*>(in), planes, exps, n_time, n_chan, c0, nc, n_inputs, ni_pad, comp_stride,
         window, exp_windows);
   else
-    unpack_cf32_digits_kernel<<<(unsigned)blocks, 256, 0, stream>>>(reinterpret_cast<const float2*>(in), planes,
+    unpack_cf32_digits_kernel<<<(unsigned)blocks, 256, 0, stream>>>(in, planes,
                                                                     exps, n_time, n_chan, c0, nc, n_inputs, ni_pad,
                                                                     comp_stride, window, exp_windows);
   return cudaGetLastError();

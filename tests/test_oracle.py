@@ -236,6 +236,61 @@ def test_cf32_against_full_matrix():
     assert np.max(np.abs(got - want)) <= 1e-12 * scale
 
 
+def float_edge_input(seed: int) -> np.ndarray:
+    """Gaussian float spectra whose stations sit at magnitudes 2^-135 (every
+    sample subnormal), 2^-100, 1 and 2^40, with a few subnormal samples inside
+    normal windows."""
+    x = synth.gaussian_cf32(50, 2, 8, seed=seed).astype(np.float64)
+    scales = np.array([2.0**-135, 2.0**-100, 1.0, 2.0**40] * 2)
+    x *= scales[None, None, :, None, None]
+    x[3, 0, 2, 1, 0] = 1e-40
+    x[7, 1, 6, 0, 1] = -3e-42
+    return x.astype(np.float32)
+
+
+def test_cf32_edge_magnitudes_against_full_matrix():
+    # subnormal and very small or large finite inputs: double holds every product exactly
+    # enough, so the oracle equals numpy's complex128 brute force to 1e-12 of each entry's
+    # Cauchy-Schwarz scale sqrt(V_ii V_jj)
+    x = float_edge_input(37)
+    assert np.count_nonzero((x != 0) & (np.abs(x) < np.finfo(np.float32).tiny)) > 200
+    xc = (x[..., 0].astype(np.float64) + 1j * x[..., 1]).reshape(50, 2, 16)
+    want = lower(full_matrix(xc))
+    got = oracle.correlate(FMT_CF32, x)
+    idx = np.arange(16)
+    autos = want[:, idx * (idx + 1) // 2 + idx, 0]
+    ii, jj = np.tril_indices(16)
+    order = np.argsort(ii * (ii + 1) // 2 + jj)
+    scale = np.sqrt(autos[:, ii[order]] * autos[:, jj[order]])
+    assert np.all(scale > 0)
+    assert np.all(np.abs(got - want).max(axis=-1) <= 1e-12 * scale)
+
+
+def test_cf32_non_finite_samples_reach_exactly_their_pairs():
+    # a NaN or an infinity at (t, c, input) makes the real part of every pair of that input
+    # in channel c non-finite (inf * x or NaN), as numpy's complex arithmetic does; every
+    # other entry stays finite and equal to the brute force
+    x = synth.gaussian_cf32(30, 2, 5, seed=41)
+    x[4, 1, 3, 0, 0] = np.nan    # channel 1, input 6
+    x[9, 0, 1, 1, 1] = np.inf    # channel 0, input 3
+    x[20, 1, 0, 1, 0] = -np.inf  # channel 1, input 1
+    got = oracle.correlate(FMT_CF32, x)
+    xc = np.empty((30, 2, 10), dtype=np.complex128)  # set apart: 1j * inf would make a NaN real part
+    xc.real = x[..., 0].reshape(30, 2, 10)
+    xc.imag = x[..., 1].reshape(30, 2, 10)
+    with np.errstate(invalid="ignore"):
+        want = lower(full_matrix(xc))
+    ii, jj = np.tril_indices(10)
+    order = np.argsort(ii * (ii + 1) // 2 + jj)
+    i, j = ii[order], jj[order]
+    bad = {0: {3}, 1: {6, 1}}
+    for c in range(2):
+        poisoned = np.isin(i, list(bad[c])) | np.isin(j, list(bad[c]))
+        assert np.all(~np.isfinite(got[c, poisoned, 0]))
+        assert np.all(np.isfinite(got[c, ~poisoned]))
+        assert np.allclose(got[c, ~poisoned], want[c, ~poisoned], rtol=1e-12, atol=1e-12)
+
+
 @pytest.mark.parametrize("fmt", [FMT_CI4, FMT_CI8, FMT_CF32])
 def test_pairs_entry_point(fmt):
     k, nc, ns = 21, 3, 4

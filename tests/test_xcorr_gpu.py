@@ -137,9 +137,9 @@ def test_dump_reset_and_wide_fold(torch, engine):
 @pytest.mark.parametrize("fmt", ["ci4", "ci8"])
 def test_input_at_any_byte_offset(torch, engine, fmt):
     # a time slice of a larger buffer starts at an arbitrary byte: the kernels
-    # take their unaligned paths and stay exact
-    if fmt == "ci8" and engine == "tensor":
-        pytest.skip("the tensor engine takes 4-bit input")
+    # take their unaligned paths and stay exact (4-bit on the tensor engine: the
+    # planes path, as the fused kernel needs 16-byte alignment; int8: the
+    # element-wise unpack into BF16 planes)
     n_time, n_chan, n_sta = 50, 2, 32
     if fmt == "ci4":
         x = synth.uniform_ci4(n_time, n_chan, n_sta, seed=31, lo=-8, hi=7)
@@ -547,7 +547,7 @@ def workload_512():
 
 
 @pytest.mark.parametrize("engine,tuning", [
-    ("tensor", (1, 0, 2, 0)),   # the fused shape the benchmark's autotuner picks
+    ("tensor", (1, 0, 2, 0)),   # the shared-memory fused kernel's shapes
     ("tensor", (0, 0, 2, 0)), ("tensor", (3, 0, 2, 0)),
     ("tensor", (4, 0, 2, 0)), ("tensor", (5, 0, 2, 0)), ("tensor", (6, 0, 2, 0)),  # A in tensor memory
     ("tensor", (7, 0, 2, 0)), ("tensor", (8, 0, 2, 0)), ("tensor", (9, 0, 2, 0)),  # CTA pairs
@@ -557,6 +557,26 @@ def test_workload_512_inputs_512_channels_2048_samples(torch, workload_512, engi
     got, _ = run(torch, workload_512, engine, tuning=tuning)
     sample_check(got, workload_512, oracle.FMT_CI4, channels=[0, 137, 511], n_pairs_sample=400,
                  seed=3)
+
+
+@pytest.mark.parametrize("variant", [4, 8])
+def test_workload_512_execute_dump_into_the_callers_buffer(torch, workload_512, variant):
+    # The benchmark's timed call: one execute_dump with reset into a device buffer the caller
+    # owns, which the fused kernel writes directly (no accumulator copy).  Twice in a row into
+    # the same buffer: the second call must store, not add.  Shape 4 is the default kernel
+    # (A operand in tensor memory), 8 the CTA-pair kernel.
+    xd = torch.from_numpy(np.ascontiguousarray(workload_512)).cuda()
+    with xcorr.Plan(256, 512, 2048) as plan:
+        plan.set_tuning(variant, 0, 2, 0)
+        out = torch.full((512, plan.info["n_pairs"], 2), -77, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            plan.execute_dump(xd, out)
+        assert plan.samples == 2048
+        plan.sync()
+        assert plan.query()["samples_integrated"] == 0
+    got = out.cpu().numpy().astype(np.int64)
+    sample_check(got, workload_512, oracle.FMT_CI4, channels=[0, 255, 511], n_pairs_sample=400,
+                 seed=5 + variant)
 
 
 def test_workload_512_host_to_host(torch, workload_512):

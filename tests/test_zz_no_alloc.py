@@ -1,4 +1,4 @@
-"""The allocation-free entry point against the plan-based path.
+"""The allocation-free entry point against the oracle and the plan-based path.
 
 ``xcorr_correlate_ci4_noalloc`` exists for callers that cannot allocate device
 memory when they correlate (a real-time capture loop, where cudaMalloc would
@@ -11,6 +11,7 @@ This file is named to run last; it passes on its own and after the rest.
 import numpy as np
 import pytest
 
+import oracle
 from paper_1401_8288_gb300 import synth, xcorr
 
 pytestmark = pytest.mark.gpu
@@ -33,23 +34,32 @@ def plan_result(torch, xd, n_sta, n_chan, n_time):
     return out.cpu().numpy()
 
 
-def test_noalloc_matches_the_plan_path_on_two_calls_in_a_row(torch):
-    # the second call is smaller and different, so stale scratch from the
-    # first would show up as a mismatch
-    cases = [(100, 16, 512, 41), (70, 24, 300, 42)]
-    for n_sta, n_chan, n_time, seed in cases:
+def noalloc_result(torch, xd, n_sta, n_chan, n_time):
+    n_pairs = 2 * n_sta * (2 * n_sta + 1) // 2
+    out = torch.full((n_chan, n_pairs, 2), -12345, dtype=torch.int32, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    xcorr.xcorr_correlate_ci4_noalloc(xd.data_ptr(), n_time, n_chan, n_sta, out.data_ptr(),
+                                      status.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    return out.cpu().numpy()
+
+
+# (stations, channels, samples, seed): 200 inputs take the byte-wise unpack; 128 inputs with a
+# 16-byte aligned buffer take the 128-bit unpack, twice with the same shape and new data, so
+# that planes left from the first call would change the second result
+CASES = [(100, 16, 512, 41), (64, 8, 1024, 42), (64, 8, 1024, 43)]
+
+
+def test_noalloc_matches_the_oracle_and_the_plan_on_calls_in_a_row(torch):
+    for n_sta, n_chan, n_time, seed in CASES:
         x = synth.gaussian_planewave_ci4(n_time, n_chan, n_sta, seed=seed)
         xd = torch.from_numpy(x).cuda()
-        n_pairs = 2 * n_sta * (2 * n_sta + 1) // 2
-        out = torch.full((n_chan, n_pairs, 2), -12345, dtype=torch.int32, device="cuda")
-        status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
-        stream = torch.cuda.current_stream().cuda_stream
-        xcorr.xcorr_correlate_ci4_noalloc(xd.data_ptr(), n_time, n_chan, n_sta, out.data_ptr(),
-                                          status.data_ptr(), stream)
-        torch.cuda.synchronize()
-        assert int(status.item()) == 0
-        want = plan_result(torch, xd, n_sta, n_chan, n_time)
-        assert np.array_equal(out.cpu().numpy(), want)
+        assert xd.data_ptr() % 16 == 0
+        got = noalloc_result(torch, xd, n_sta, n_chan, n_time)
+        assert np.array_equal(got.astype(np.int64), oracle.correlate(oracle.FMT_CI4, x)), (n_sta, seed)
+        assert np.array_equal(got, plan_result(torch, xd, n_sta, n_chan, n_time)), (n_sta, seed)
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch(torch):
@@ -60,3 +70,7 @@ def test_noalloc_refuses_sizes_beyond_its_scratch(torch):
         xcorr.xcorr_correlate_ci4_noalloc(x.data_ptr(), 8192, 64, 512, out.data_ptr())
     assert e.value.status == 1  # INVALID_ARG
     assert "scratch" in str(e.value)
+    with pytest.raises(xcorr.XcorrError) as e:
+        # a station count whose input count would overflow an int is refused before any arithmetic
+        xcorr.xcorr_correlate_ci4_noalloc(x.data_ptr(), 1, 1, 2**30 + 1, out.data_ptr())
+    assert e.value.status == 1
