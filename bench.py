@@ -53,7 +53,14 @@ WORKLOADS = {
     # 24 independent subarrays of uneven size in one launch (see batch_arm)
     "batch24": dict(name="24 subarrays, inputs 16..704, channels 64..1024, K 512..8192, 4+4-bit",
                     seed=14018288 + 4, fmt="ci4", dtype="e4m3"),
+    # many small subarrays, where per-instance launches leave most SMs idle
+    "batch_small": dict(name="64 subarrays, inputs 16..128, channels 16..256, K 512..4096, 4+4-bit",
+                        seed=14018288 + 7, fmt="ci4", dtype="e4m3",
+                        mix=dict(count=64, inputs=(16, 128), channels=(16, 256), samples=(512, 4096))),
     # the streaming server: F-engine packets -> device ring -> X-stage -> dumps (see stream_arm)
+    # the engine choice for small problems: both engines over a grid of small sizes (see sweep_arm)
+    "engine_sweep": dict(name="4-bit, inputs 2..256, channels 16..256, K 256..2048: tensor (default and "
+                              "small-problem shapes) vs CUDA-core", seed=14018288 + 6, fmt="ci4", dtype="e4m3"),
     "stream1024": dict(name="1024 inputs (512 stations x 2 pols), 1024 channels, K=8192 per dump, "
                             "4+4-bit Gaussian in 8 KB packets (4 samples x 128 channels x 16 "
                             "inputs) + 16 B header, ring of 4 blocks of 2048 samples",
@@ -68,7 +75,7 @@ KERNEL_SOURCES = {
     "xcorr_tc_fused_kernel": ("xcorr_tc_fused.cu", "fused_common.cuh", "sm103_ptx.cuh", "xcorr_internal.h"),
     "xcorr_tc_kernel": ("xcorr_tc.cu", "sm103_ptx.cuh", "xcorr_internal.h"),
 }
-FUSED_TA_VARIANTS = (4, 5, 6)  # tuning stage_variants served by the tensor-memory-A fused kernel
+FUSED_TA_VARIANTS = (4, 5, 6, 10)  # tuning stage_variants served by the tensor-memory-A fused kernel
 FUSED_PAIR_VARIANTS = (7, 8, 9)  # ... and by the CTA-pair kernel
 
 
@@ -93,8 +100,14 @@ def parse_args():
                     help="keep the library's default launch shape")
     ap.add_argument("--tuning", default="",
                     help="fix the launch shape instead of autotuning: variant,groups,x_streams")
+    ap.add_argument("--tuning-cache", default="",
+                    help="JSON-lines tuning cache to load before and save after (batch workloads)")
     ap.add_argument("--sustained-s", type=float, default=2.5,
                     help="seconds of back-to-back steps for the sustained record (0 = skip)")
+    ap.add_argument("--graph", type=int, default=0, metavar="STEPS",
+                    help="capture STEPS steps in one CUDA graph and time its replays (no host call per "
+                         "step: for small workloads whose kernels are shorter than the host's calls); "
+                         "--steps must be a multiple of STEPS")
     return ap.parse_args()
 
 
@@ -300,13 +313,16 @@ def reference_arm(args) -> int:
     import oracle
     from paper_1401_8288_gb300 import costmodel
     oracle.build()
-    if args.workload == "batch24":
+    if args.workload in ("batch24", "batch_small"):
         emit({"impl": "reference", "unavailable": "the oracle arm times single workloads; "
               "run it per subarray size"})
         return 0
     if args.workload == "stream1024":
         emit({"impl": "reference", "unavailable": "the oracle has no packet path; its correlation "
               "rate is the reference line of the default workload"})
+        return 0
+    if args.workload == "engine_sweep":
+        emit({"impl": "reference", "unavailable": "the sweep compares the library's own engines"})
         return 0
     w = WORKLOADS[args.workload]
     x = make_input(w, w["seed"])
@@ -342,8 +358,11 @@ def reference_arm(args) -> int:
 
 # ----------------------------------------------------------------- batch --
 def batch_arm(args) -> int:
-    """Many uneven subarrays: one persistent launch per step, replayed as a
-    CUDA graph, against the same subarrays run as separate plans."""
+    """Many uneven subarrays: one execute of a batch per step (a fused launch per
+    shape class, the classes side by side), replayed as a CUDA graph, against
+    the same subarrays run as separate plans (per-instance launches), eagerly
+    and from one graph.  Every subarray and plan is autotuned through the
+    tuning cache (--tuning-cache)."""
     import torch
 
     from paper_1401_8288_gb300 import dist
@@ -353,8 +372,10 @@ def batch_arm(args) -> int:
     __graft_entry__.build()
     from paper_1401_8288_gb300 import costmodel, synth, xcorr
 
-    w = WORKLOADS["batch24"]
-    subs = synth.subarray_batch(w["seed"])
+    w = WORKLOADS[args.workload]
+    if args.tuning_cache and os.path.exists(args.tuning_cache):
+        xcorr.xcorr_tuning_cache_load(args.tuning_cache)
+    subs = synth.subarray_batch(w["seed"], **w.get("mix", {}))
     sizes = [(s["n_sta"], s["n_chan"], s["n_time"]) for s in subs]
     xs = [synth.uniform_ci4_torch(nt, nc, ns, seed=s["seed"] + info.rank) for (ns, nc, nt), s in zip(sizes, subs)]
     cmacs = sum(costmodel.cmacs(nc, nt, 2 * ns) for ns, nc, nt in sizes)
@@ -373,25 +394,36 @@ def batch_arm(args) -> int:
         return dist.max_over_ranks(ev0.elapsed_time(ev1), torch.device("cuda", info.local_rank)) / steps
 
     batch = xcorr.Batch(sizes)
-    # autotuner over the batch launch's shapes (0-2 planes path, 3-5 fused kernel), by replay time
-    best = None
+    # batch-wide shapes (0-2 planes path, 3-5 fused kernel), by replay time
+    wide = {}
     for v in range(6):
         try:
             batch.set_variant(v)
         except xcorr.XcorrError:  # a fused shape for subarrays the fused kernel does not take
             continue
         batch.capture(xs)
-        ms = timed(batch.replay, 3)
-        if best is None or ms < best[1]:
-            best = (v, ms)
-    batch.set_variant(best[0])
+        wide[v] = timed(batch.replay, 3)
+    # a shape per subarray (its size class), timed alone or taken from the tuning cache
+    per_sub = batch.autotune(xs)
+    batch.capture(xs)
+    ms_classes = timed(batch.replay, 3)
+    best_wide = min(wide, key=wide.get)
+    if wide[best_wide] < ms_classes:
+        batch.set_variant(best_wide)
+        chosen = {"kind": "one shape for the batch", "stage_variant": best_wide}
+    else:
+        chosen = {"kind": "a shape per subarray (size class): tensor-memory-A shapes 4-6 share one launch "
+                          "per shape, other shapes run their subarray alone, all side by side",
+                  "subarrays_per_shape": {str(v): per_sub.count(v) for v in sorted(set(per_sub))}}
     batch.capture(xs)
     with ClockSampler(info.local_rank) as clocks:
         ms_graph = timed(batch.replay, args.steps)
     batch.sync()
     outs = batch.outputs
-    # the same subarrays as separate plans, one after another
+    # the same subarrays as separate plans (each autotuned), one after another
     plans = [xcorr.Plan(ns, nc, nt) for ns, nc, nt in sizes]
+    for p, x in zip(plans, xs):
+        p.autotune(x, cached=True)
     per_out = [torch.empty_like(o) for o in outs]
 
     def each():
@@ -400,26 +432,125 @@ def batch_arm(args) -> int:
 
     ms_each = timed(each, max(2, args.steps // 4))
     same = all(torch.equal(a, b) for a, b in zip(outs, per_out))
+    each()
+    torch.cuda.synchronize()
+    g_each = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_each):
+        each()
+    ms_each_graph = timed(g_each.replay, max(2, args.steps // 4))
+    same = same and all(torch.equal(a, b) for a, b in zip(outs, per_out))
+    # one subarray of each size against the oracle (whole first channel + sampled pairs)
+    check = []
+    for k in sorted({0, len(sizes) // 2, len(sizes) - 1}):
+        check.append(oracle_check(outs[k].cpu().numpy(), xs[k].cpu().numpy(), "ci4", [0], 100,
+                                  seed=w["seed"] + k))
+    del g_each
     for p in plans:
         p.close()
     batch.close()
+    if args.tuning_cache:
+        xcorr.xcorr_tuning_cache_save(args.tuning_cache)
     value = info.world * cmacs / (ms_graph * 1e-3) / 1e12
+    exact = all(c["exact"] for c in check) and same
     if info.rank == 0:
         emit({"metric": METRIC, "value": value, "unit": "TCMAC/s", "n_gpus": info.world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3",
               "data": "synthetic",
-              "config": {"workload": w["name"], "subarrays": sizes, "stage_variant": best[0],
-                         "engine": ("fused 4-bit kernel, A operand in tensor memory, one launch over all "
-                                    "subarrays' tile pairs") if best[0] >= 3 else
-                                   "unpack per subarray + one planes X launch",
+              "config": {"workload": w["name"], "subarrays": sizes, "shape": chosen,
+                         "per_subarray_shapes": per_sub,
+                         "batch_wide_ms": {str(v): ms for v, ms in wide.items()}, "per_class_ms": ms_classes,
+                         "engine": ("fused 4-bit kernels on the raw input, launched side by side"
+                                    if best_wide >= 3 or wide[best_wide] >= ms_classes
+                                    else "unpack per subarray + one planes X launch"),
                          "graph": True, "cmacs_per_step_per_gpu": cmacs,
-                         "l2": "inputs larger than L2 (15.2 GB in, 7.5 GB out per step)"},
+                         "l2": "inputs larger than L2" if cmacs > 1e11 else "working set partly in L2"},
               "per_instance": {"value": info.world * cmacs / (ms_each * 1e-3) / 1e12,
                                "unit": "TCMAC/s", "ms_per_step": ms_each,
                                "batch_speedup": ms_each / ms_graph, "outputs_identical": same},
-              "gpu_launches": (1 if best[0] >= 3 else len(sizes) + 1) * args.steps,
+              "per_instance_graph": {"value": info.world * cmacs / (ms_each_graph * 1e-3) / 1e12,
+                                     "unit": "TCMAC/s", "ms_per_step": ms_each_graph,
+                                     "batch_speedup": ms_each_graph / ms_graph},
+              "exact": exact, "parity": check,
+              "gpu_launches": (len({v for v in per_sub if 4 <= v <= 6}) + sum(1 for v in per_sub if not 4 <= v <= 6))
+                              * args.steps if "subarrays_per_shape" in chosen else
+                              (1 if best_wide >= 3 else len(sizes) + 1) * args.steps,
               "clocks": clocks.summary()})
+    dist.barrier()
+    return 0 if exact else 1
+
+
+# ---------------------------------------------------------- engine sweep --
+def sweep_arm(args) -> int:
+    """Per-call device time of one execute_dump (inputs in HBM) for the tensor
+    engine at its default shape (4) and its small-problem shape (10), and for
+    the CUDA-core engine, over small problem sizes: the evidence behind
+    XCORR_ENGINE_AUTO and the default shape of a plan.  Achieved HBM GB/s =
+    (input + output bytes) / time."""
+    import torch
+
+    from paper_1401_8288_gb300 import dist
+    info = dist.init("nccl")
+    torch.cuda.set_device(info.local_rank)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1401_8288_gb300 import costmodel, synth, xcorr
+
+    rows = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 20)
+    for n_in in (2, 8, 16, 32, 64, 128, 256):
+        for n_chan in (16, 64, 256):
+            for n_time in (256, 1024, 2048):
+                xd = synth.uniform_ci4_torch(n_time, n_chan, n_in // 2, seed=n_in * 7 + n_chan + n_time)
+                n_pairs = costmodel.n_pairs(n_in)
+                out = torch.empty((n_chan, n_pairs, 2), dtype=torch.int32, device="cuda")
+                row = {"n_inputs": n_in, "n_channels": n_chan, "n_time": n_time}
+                for label, engine, tuning in (("tensor_default", "tensor", None), ("tensor_small", "tensor", 10),
+                                              ("cuda_core", "cuda_core", None)):
+                    with xcorr.Plan(n_in // 2, n_chan, n_time, engine=engine) as plan:
+                        if tuning is not None:
+                            plan.set_tuning(tuning, 0, 2, 0)
+                        for _ in range(max(args.warmup, 3)):
+                            plan.execute_dump(xd, out)
+                        torch.cuda.synchronize()
+                        ev0.record()
+                        for _ in range(reps):
+                            plan.execute_dump(xd, out)
+                        ev1.record()
+                        torch.cuda.synchronize()
+                        row[label + "_eager_us"] = round(1e3 * ev0.elapsed_time(ev1) / reps, 2)
+                        # the same call, 20 times in one CUDA graph: the device's own time per call
+                        graph = torch.cuda.CUDAGraph()
+                        with torch.cuda.graph(graph):
+                            for _ in range(20):
+                                plan.execute_dump(xd, out)
+                        for _ in range(2):
+                            graph.replay()
+                        torch.cuda.synchronize()
+                        n_rep = max(1, reps // 20)
+                        ev0.record()
+                        for _ in range(n_rep):
+                            graph.replay()
+                        ev1.record()
+                        torch.cuda.synchronize()
+                        row[label + "_us"] = round(1e3 * ev0.elapsed_time(ev1) / (20 * n_rep), 2)
+                        plan.sync()
+                        del graph
+                nbytes = xd.numel() + out.numel() * 4
+                best = min(("tensor_default", "tensor_small", "cuda_core"), key=lambda k: row[k + "_us"])
+                row["best"] = best
+                row["best_hbm_gbs"] = round(nbytes / (row[best + "_us"] * 1e-6) / 1e9, 1)
+                row["tcmacs_best"] = round(costmodel.cmacs(n_chan, n_time, n_in) / (row[best + "_us"] * 1e-6) / 1e12, 4)
+                rows.append(row)
+    if info.rank == 0:
+        emit({"metric": "per-call time of one execute_dump by engine over small sizes", "unit": "us",
+              "n_gpus": info.world, "steps": reps, "warmup": args.warmup, "higher_is_better": False,
+              "data": "synthetic", "config": {"workload": WORKLOADS["engine_sweep"]["name"],
+                                              "timing": "CUDA events around back-to-back replays of a graph of "
+                                                        "20 calls (<engine>_us, per call) and around eager "
+                                                        "calls (<engine>_eager_us); inputs in HBM"},
+              "rows": rows})
     dist.barrier()
     return 0
 
@@ -467,27 +598,45 @@ def our_arm(args) -> int:
     out_dtype = torch.float32 if fmt == "cf32" else torch.int32
     out = torch.empty((n_chan, n_pairs, 2), dtype=out_dtype, device=dev)
 
-    def step():
+    def eager_step():
         plan.execute_dump(xd, out, reset=True)
 
     for _ in range(max(args.warmup, 3)):
-        step()
+        eager_step()
     torch.cuda.synchronize()
+    if args.graph:  # args.graph steps recorded once; the timed loop replays the graph
+        if args.steps % args.graph:
+            raise SystemExit("--steps must be a multiple of --graph")
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(args.graph):
+                eager_step()
+        replays = args.steps // args.graph
+        for _ in range(max(args.warmup, 3)):
+            graph.replay()
+        torch.cuda.synchronize()
+    else:
+        replays = args.steps
+        step = eager_step
 
-    xcorr.xcorr_profile_enable(plan.handle, args.steps)
+    if not args.graph:
+        xcorr.xcorr_profile_enable(plan.handle, args.steps)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(info.local_rank) as clocks:
         dist.barrier()
         torch.cuda.synchronize()
         ev0.record()
-        for _ in range(args.steps):
-            step()
+        for _ in range(replays):
+            graph.replay() if args.graph else step()
         ev1.record()
         torch.cuda.synchronize()
         dist.barrier()
     ms_total = ev0.elapsed_time(ev1)
-    kernel_ms = xcorr.xcorr_profile_read(plan.handle, args.steps)
-    xcorr.xcorr_profile_enable(plan.handle, 0)
+    if args.graph:  # no per-launch events inside a graph: the replay time bounds the kernels' time
+        kernel_ms = [(0.0, ms_total / args.steps)] * args.steps
+    else:
+        kernel_ms = xcorr.xcorr_profile_read(plan.handle, args.steps)
+        xcorr.xcorr_profile_enable(plan.handle, 0)
     ms_total = dist.max_over_ranks(ms_total, dev)
     value = info.world * cmacs_per_step * args.steps / (ms_total * 1e-3) / 1e12
     # the last timed step's output against the oracle (outside the timed region)
@@ -496,7 +645,7 @@ def our_arm(args) -> int:
 
     # sustained: the same step back to back for a few seconds, with its own clock record
     sustained = None
-    if args.sustained_s > 0:
+    if args.sustained_s > 0 and not args.graph:
         n_sus = max(100, int(args.sustained_s / (ms_total / args.steps * 1e-3)))
         xcorr.xcorr_profile_enable(plan.handle, 512)  # kernel times of the last 512 steps
         with ClockSampler(info.local_rank) as sus_clocks:
@@ -585,6 +734,12 @@ def our_arm(args) -> int:
                                                 "(MEASURED_PEAKS.json); of measured"
                                                 if "bf16_tflops_sustained" in peaks else "of fallback"}
 
+    hbm = {"bytes_per_step": in_bytes + out_bytes,
+           "achieved_gbs": (in_bytes + out_bytes) / (x_ms * 1e-3) / 1e9,
+           "peak_gbs": peaks.get("hbm_gbs", 6800.0),
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs; of measured" if "hbm_gbs" in peaks else "of fallback"}
+    hbm["frac"] = hbm["achieved_gbs"] / hbm["peak_gbs"]
+
     result = {
         "metric": METRIC,
         "value": value,
@@ -636,10 +791,13 @@ def our_arm(args) -> int:
                      "peak_source": peak_note,
                      "frac_of_probe_peak": achieved / (peak_e4m3 if fmt == "ci4" else peak_e4m3 / 2)},
         "exact": parity["exact"] and e2e_parity["exact"],
+        "hbm_view": hbm,
         "parity": {"timed_output": parity, "e2e_output": e2e_parity},
         "e2e": {"value": e2e_value, "unit": "TCMAC/s", "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": out_bytes, "ms_per_step": e2e_ms / args.steps},
         "gpu_launches": launches_per_step * args.steps,
+        "timing": (f"CUDA graphs of {args.graph} steps replayed (kernel_ms_per_step is the replay time per "
+                   "step)" if args.graph else "eager calls; kernel times from events recorded around each launch"),
         "clocks": clocks.summary(),
         "sustained": sustained,
         # GB300 keeps no tcgen05 int8 kind; its int8 tensor path is warp-level mma.sync s8,
@@ -812,10 +970,12 @@ def main() -> int:
     args = parse_args()
     if args.impl == "reference":
         return reference_arm(args)
-    if args.workload == "batch24":
+    if args.workload in ("batch24", "batch_small"):
         return batch_arm(args)
     if args.workload == "stream1024":
         return stream_arm(args)
+    if args.workload == "engine_sweep":
+        return sweep_arm(args)
     return our_arm(args)
 
 

@@ -88,7 +88,9 @@ typedef enum {
 typedef enum { XCORR_IN_CI4 = 0, XCORR_IN_CI8 = 1, XCORR_IN_CF32 = 2 } xcorr_in_fmt;
 
 typedef enum {
-    XCORR_ENGINE_AUTO = 0,      /* tensor cores where the format has a tensor path       */
+    XCORR_ENGINE_AUTO = 0,      /* the faster engine as measured on GB300: CUDA-core for
+                                   integer input with fewer than 16 inputs and at most 16
+                                   channels, the tensor cores otherwise                   */
     XCORR_ENGINE_TENSOR = 1,    /* tcgen05 tensor-core X kernel                          */
     XCORR_ENGINE_CUDA_CORE = 2  /* plain CUDA-core (dp4a) X kernel, integer formats only */
 } xcorr_engine;
@@ -107,7 +109,7 @@ typedef struct xcorr_plan_s *xcorr_plan;
 
 /* Launch shape of the tensor-core path (xcorr_plan_set_tuning, xcorr_autotune). */
 typedef struct {
-    int stage_variant;  /* shared-memory ring, 0 .. 9: planes path 0 = 3 x 64 KB, 1 (and 3 .. 9)
+    int stage_variant;  /* shared-memory ring, 0 .. 10: planes path 0 = 3 x 64 KB, 1 (and 3 .. 10)
                            = 4 x 48 KB, 2 = 6 x 32 KB stages; fused path see `unfused`         */
     int groups;         /* channel groups whose unpack overlaps the X kernel; 0 = automatic (<= 8) */
     int x_streams;      /* 1 or 2 streams the groups' X launches alternate over                 */
@@ -121,6 +123,11 @@ typedef struct {
                            default of a 4-bit plan); 7 .. 9: pairs of SMs (a thread-block
                            cluster of 2, one cta_group::2 MMA) sharing a column tile,
                            rings of 96 x (2 + 3), 128 x (2 + 2), 96 x (2 + 4) samples;
+                           10: the tensor-memory-A kernel's small-problem layout,
+                           128 x (2 + 2): for N_i <= 64, 128 / N_i channels side by
+                           side in one 128-row tile; and when a launch has fewer tiles
+                           than SMs, each tile's stages split over several CTAs whose
+                           sums are added atomically into the (cleared) output;
                            1 = always through E4M3 planes in HBM                            */
 } xcorr_tuning;
 
@@ -142,8 +149,13 @@ typedef struct {
  * Create a plan.  Validates cfg, allocates the device accumulator and any
  * staging buffers on the current device (the plan owns them), and selects the
  * kernels.  *out receives the plan, or NULL on failure.
- * Engines: AUTO and TENSOR use the tcgen05 kernels for every format (4-bit as
- * E4M3, int8 as BF16, float as three BF16 pieces); CUDA_CORE takes CI4 / CI8.
+ * Engines: TENSOR uses the tcgen05 kernels for every format (4-bit as E4M3,
+ * int8 as BF16, float as three BF16 pieces); CUDA_CORE takes CI4 / CI8; AUTO
+ * takes CUDA_CORE for integer input with fewer than 16 inputs and at most 16
+ * channels (where its single launch was measured faster than the tensor
+ * path's unpack + X) and TENSOR otherwise.  A 4-bit tensor plan starts on
+ * launch shape 10 (the small-problem layout) when N_i <= 64 and either
+ * max_time_per_exec >= 1024 or n_channels >= 256, else on shape 4.
  * max_integration (xcorr_plan_query) is 16,777,215 samples for CI4, 65,535
  * for CI8 (exact int32) and 16,777,216 for CF32 (longer sums: dump with
  * XCORR_DUMP_ADD_WIDE into double).
@@ -237,7 +249,7 @@ xcorr_status xcorr_watchdog_selftest(xcorr_plan plan, void *stream);
 
 /*
  * Fix the tensor path's launch shape (results do not depend on it).
- * Errors: INVALID_ARG (stage_variant not in [0, 9], groups not in [0, 8],
+ * Errors: INVALID_ARG (stage_variant not in [0, 10], groups not in [0, 8],
  * x_streams not 1 or 2), DEVICE.
  */
 xcorr_status xcorr_plan_set_tuning(xcorr_plan plan, const xcorr_tuning *tuning);
@@ -251,6 +263,36 @@ xcorr_status xcorr_plan_set_tuning(xcorr_plan plan, const xcorr_tuning *tuning);
  */
 xcorr_status xcorr_autotune(xcorr_plan plan, const void *d_in, int n_time, void *stream,
                             xcorr_tuning *best, float *best_ms);
+
+/*
+ * The autotuner with a cache of its results (the paper has no counterpart; the
+ * paper's deployment retunes nothing, but a correlator serving many subarray
+ * sizes should not time every shape at every start).  If the process's tuning
+ * cache holds a shape for this plan's problem -- the device's name and SM
+ * count, the input format, N_i, the channel count and n_time -- the shape is
+ * applied without timing and *from_cache is 1; otherwise xcorr_autotune runs
+ * and its winner is recorded in the cache (*from_cache 0).  Either way the
+ * plan's current integration is discarded, as by xcorr_autotune.  best,
+ * best_ms (the recorded time) and from_cache may be NULL.
+ * Errors: as xcorr_autotune.
+ */
+xcorr_status xcorr_autotune_cached(xcorr_plan plan, const void *d_in, int n_time, void *stream,
+                                   xcorr_tuning *best, float *best_ms, int *from_cache);
+
+/*
+ * The process's tuning cache, in files.  save writes every entry, one JSON
+ * object per line with the fields scope ("plan" or "batch"), device, sms, fmt,
+ * n_inputs, n_channels, n_time, stage_variant, groups, x_streams, unfused and
+ * us (the recorded time, microseconds); the file is replaced whole (written
+ * to path.tmp, then renamed).  load merges a file's entries into the cache
+ * (an entry for the same problem is replaced); a line without every field,
+ * or with a value out of range, is skipped and counted in *n_skipped.  clear
+ * empties the cache.  n_loaded, n_skipped and n_saved may be NULL.
+ * Errors: INVALID_ARG (NULL path, a file that cannot be opened or written).
+ */
+xcorr_status xcorr_tuning_cache_load(const char *path, int *n_loaded, int *n_skipped);
+xcorr_status xcorr_tuning_cache_save(const char *path, int *n_saved);
+xcorr_status xcorr_tuning_cache_clear(void);
 
 /* Describe the plan.  Errors: INVALID_ARG. */
 xcorr_status xcorr_plan_query(xcorr_plan plan, xcorr_plan_info *info);
@@ -347,6 +389,32 @@ xcorr_status xcorr_batch_create(xcorr_batch *out, const xcorr_config *cfgs, int 
  * of a batch that qualifies).  Errors: INVALID_ARG, UNSUPPORTED (a fused shape
  * for a batch that does not qualify), OOM (the planes of a planes shape). */
 xcorr_status xcorr_batch_set_variant(xcorr_batch batch, int stage_variant);
+
+/* A shape per subarray (fused batches only): variants[s] is a 4-bit plan
+ * shape, xcorr_tuning.stage_variant 0 .. 10 with unfused = 0.  Subarrays whose
+ * shape is one of the tensor-memory-A kernel's (4, 5, 6) form a class with its
+ * own item list and one shared launch; a subarray with any other shape (the
+ * CTA-pair kernel 7-9, the small-problem layout 10, the shared-memory kernel
+ * 0-3) runs as its own launch.  All of these run side by side on internal
+ * streams forked from (and joined back to) the caller's stream, inside a
+ * captured graph too.  xcorr_batch_set_variant(3 + k) sets every subarray to
+ * plan shape 4 + k.  get reads the current shapes (the batch-wide shape 0-2,
+ * repeated, for the planes path).  Errors: INVALID_ARG, UNSUPPORTED (a batch
+ * the fused kernel does not take). */
+xcorr_status xcorr_batch_set_subarray_variants(xcorr_batch batch, const int *variants);
+xcorr_status xcorr_batch_get_subarray_variants(xcorr_batch batch, int *variants);
+
+/* Autotuner of a batch (the paper has no counterpart): per subarray, the
+ * fused plan shape (0 .. 10) that runs it fastest on its own, timed with these
+ * buffers (three runs each, the first as warm-up; d_outs are overwritten), or
+ * taken without timing from the process's tuning cache (scope "batch", see
+ * xcorr_tuning_cache_save), where every new result is recorded.  The shapes
+ * are applied as by xcorr_batch_set_subarray_variants and written to
+ * variants (n entries; may be NULL).  A batch on the planes path has one
+ * shape and nothing to tune.  Synchronises the stream.  Errors: INVALID_ARG
+ * (NULL or unaligned buffers), CUDA, DEVICE. */
+xcorr_status xcorr_batch_autotune(xcorr_batch batch, const void *const *d_ins, void *const *d_outs, void *stream,
+                                  int *variants);
 
 /* One batch execute on the stream.  Errors: INVALID_ARG (a NULL buffer, or an
  * input the fused kernel cannot read: not 16-byte aligned), CUDA. */

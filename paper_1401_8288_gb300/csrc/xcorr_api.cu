@@ -282,7 +282,13 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
   if (c.engine != XCORR_ENGINE_AUTO && c.engine != XCORR_ENGINE_TENSOR && c.engine != XCORR_ENGINE_CUDA_CORE)
     return fail(XCORR_ERR_INVALID_ARG, "unknown engine");
 
-  const int engine = c.engine == XCORR_ENGINE_AUTO ? XCORR_ENGINE_TENSOR : c.engine;
+  // AUTO: the engine the per-call device times favour (graph-replayed execute_dump, 4-bit input,
+  // inputs 2-256, channels 16-256, K 256-2048): the CUDA-core kernel only where the problem is
+  // smaller than one tensor tile on both sides, fewer than 16 inputs (the tensor path then unpacks
+  // to planes first: two launches) and at most 16 channels; the tensor cores everywhere else.
+  const int engine = c.engine != XCORR_ENGINE_AUTO ? c.engine
+                     : (c.fmt != XCORR_IN_CF32 && 2 * c.n_stations < 16 && c.n_channels <= 16) ? XCORR_ENGINE_CUDA_CORE
+                                                                                            : XCORR_ENGINE_TENSOR;
   if (engine == XCORR_ENGINE_CUDA_CORE && c.fmt == XCORR_IN_CF32)
     return fail(XCORR_ERR_UNSUPPORTED, "the CUDA-core engine takes integer input only");
 
@@ -338,8 +344,12 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
   plan->window_samples = c.fmt == XCORR_IN_CI4 ? xc::kTcWindowCI4 : xc::kTcWindowBF16;
   plan->exp_windows = exp_windows;
   // 4-bit input starts on the fused kernel with the A operand in tensor memory (the fastest
-  // shape measured); the planes path reads the same tuning as its 4 x 48 KB ring
-  plan->tune_variant = c.fmt == XCORR_IN_CI4 ? xc::kDefaultFusedVariant : 0;
+  // shape measured), in its small-problem layout where that measured faster: at most 64 inputs
+  // (channels packed per tile) with 1024 or more samples per execute or 256 or more channels;
+  // the planes path reads the same tuning as its 4 x 48 KB ring
+  plan->tune_variant = c.fmt != XCORR_IN_CI4 ? 0
+                       : (n_inputs <= 64 && (c.max_time_per_exec >= 1024 || c.n_channels >= 256)) ? xc::kSmallFusedVariant
+                                                                                                   : xc::kDefaultFusedVariant;
 
   if ((e = cudaMalloc(&plan->acc, acc_bytes)) != cudaSuccess ||
       (planes_bytes && (e = cudaMalloc(&plan->planes, planes_bytes)) != cudaSuccess) ||
@@ -442,12 +452,12 @@ xcorr_status xcorr_execute_dump(xcorr_plan plan, const void* d_in, int n_time, v
     return xcorr_dump(plan, out, out_on_device, flags, stream, n_samples);
   }
   // This execute is the whole integration and it is not kept: the X kernel
-  // writes it straight into the caller's buffer and the plan stays reset.
+  // writes it straight into the caller's buffer and the plan stays reset.  (No
+  // copy of the status word follows, which would put a copy between every two
+  // kernels of back-to-back calls: a kernel failure is reported by xcorr_sync.)
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   st = run_execute(plan, d_in, n_time, out, true, s);
   if (st != XCORR_OK) return st;
-  cudaError_t e = cudaMemcpyAsync(plan->status_host, plan->status, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cuda_fail(e, "status copy");
   if (n_samples) *n_samples = n_time;
   return XCORR_OK;
 }
@@ -671,6 +681,35 @@ xcorr_status xcorr_autotune(xcorr_plan plan, const void* d_in, int n_time, void*
   if (st != XCORR_OK) return st;
   if (best) *best = winner;
   if (best_ms) *best_ms = winner_ms;
+  return XCORR_OK;
+}
+
+xcorr_status xcorr_autotune_cached(xcorr_plan plan, const void* d_in, int n_time, void* stream, xcorr_tuning* best,
+                                   float* best_ms, int* from_cache) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  if (!d_in || n_time < 1 || n_time > plan->cfg.max_time_per_exec)
+    return fail(XCORR_ERR_INVALID_ARG, "d_in must be set and n_time in [1, max_time_per_exec]");
+  if (from_cache) *from_cache = 0;
+  if (plan->engine != XCORR_ENGINE_TENSOR) return xcorr_autotune(plan, d_in, n_time, stream, best, best_ms);
+  const xc::TuneKey key = xc::tune_key("plan", plan->cfg.fmt, plan->n_inputs, plan->cfg.n_channels, n_time);
+  xcorr_tuning t{};
+  float ms = 0.f;
+  if (xc::tune_cache_get(key, &t, &ms)) {
+    st = xcorr_plan_set_tuning(plan, &t);
+    if (st != XCORR_OK) return st;
+    plan->samples = 0;  // as the timed path: the plan starts a new integration
+    plan->fresh = true;
+    if (best) *best = t;
+    if (best_ms) *best_ms = ms;
+    if (from_cache) *from_cache = 1;
+    return XCORR_OK;
+  }
+  st = xcorr_autotune(plan, d_in, n_time, stream, &t, &ms);
+  if (st != XCORR_OK) return st;
+  xc::tune_cache_put(key, t, ms);
+  if (best) *best = t;
+  if (best_ms) *best_ms = ms;
   return XCORR_OK;
 }
 

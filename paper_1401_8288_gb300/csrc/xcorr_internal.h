@@ -31,8 +31,9 @@ constexpr int kTcWindowBF16 = 384;
 // stays below 2^24 for T <= 37,282; rounded down to a multiple of 384 (every stage height).
 constexpr int kFusedWindowCI4 = 37248;
 constexpr int kTcVariants = 3;     // planes-path stage shapes: 64 KB x 3, 48 KB x 4, 32 KB x 6
-constexpr int kFusedVariants = 10;  // fused 4-bit kernel shapes (the tuning's stage_variant range)
+constexpr int kFusedVariants = 11;  // fused 4-bit kernel shapes (the tuning's stage_variant range)
 constexpr int kDefaultFusedVariant = 4;  // 4-bit plans before any tuning: A in tensor memory, 128 x (2 + 2)
+constexpr int kSmallFusedVariant = 10;   // ... for small problems: the same kernel, channels packed, time split
 // The planes path's shape for a tuning's stage_variant (3 exists only for the fused kernel).
 inline int planes_variant(int v) { return v >= kTcVariants ? 1 : v; }
 constexpr int64_t kMaxIntegrationCF32 = INT64_C(16777216);  // FP32 per dump, widen beyond
@@ -185,6 +186,16 @@ cudaError_t launch_xcorr_cuda_core(int fmt, const void* in, int n_time, int n_ch
 // Choose the CUDA-core kernel's split of the time axis (1 = no split).
 int cuda_core_ksplit(int n_time, int n_chan, int n_inputs, int num_sms);
 
+// The autotuners' cache (xcorr_tune_cache.cpp): a problem's key on the current device, and the
+// shape recorded for it.
+struct TuneKey {
+  std::string scope, device;  // "plan" or "batch"; the device's name
+  int sms = 0, fmt = 0, n_inputs = 0, n_channels = 0, n_time = 0;
+};
+TuneKey tune_key(const char* scope, int fmt, int n_inputs, int n_channels, int n_time);
+bool tune_cache_get(const TuneKey& key, xcorr_tuning* tuning, float* ms);
+void tune_cache_put(const TuneKey& key, const xcorr_tuning& tuning, float ms);
+
 // Record the calling thread's error message (read by xcorr_last_error) and return st.
 xcorr_status set_error(xcorr_status st, const std::string& msg);
 // For the library's other front ends (streams): the plan checks of every call,
@@ -212,6 +223,11 @@ bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inp
 // prefetches).
 bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int row_chans, int n_time,
                          int box_t, std::string* err, int box_i = 128);
+// The same input with channel and input merged into one dimension (boxes of 128 bytes: 128 /
+// n_inputs channels side by side per time row), for the small-problem layout that packs
+// channels into one tile (n_inputs % 16 == 0, 16-byte aligned pointer).
+bool encode_raw_ci4_packed_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int row_chans,
+                                int n_time, int box_t, std::string* err);
 // The fused 4-bit X kernel (unpack on chip, offset-binary operands): one
 // launch per kFusedWindowCI4 samples; n_inputs % 16 == 0, `in` 16-byte aligned.
 int fused_stage_samples(int variant);
@@ -219,7 +235,8 @@ int fused_launches(int n_time);
 // `in` points at the first of n_chan channels; time rows hold row_chans channels.
 // Variants 0-3 decode both operands into shared memory; 4-6 run the kernel
 // with the A operand in tensor memory (its variants 0-2); 7-9 run the CTA-pair
-// kernel (its variants 0-2).
+// kernel (its variants 0-2); 10 runs the tensor-memory-A kernel's small-problem
+// layout (its variant 3: channels packed per tile, time split over the SMs).
 cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                       int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
                                       cudaStream_t stream);

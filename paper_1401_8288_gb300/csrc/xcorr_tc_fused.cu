@@ -480,6 +480,7 @@ cudaError_t launch_fused(const CUtensorMap& raw_map, const FParams& p, int grid,
 // sharing a column tile).  Deeper raw rings hide more TMA latency, deeper decoded rings more
 // decoder jitter, more decoder warps more of the decode's latency.
 int fused_stage_samples(int variant) {
+  if (variant == 10) return fused_ta_stage_samples(3);
   if (variant >= 7) return fused_pair_stage_samples(variant - 7);
   if (variant >= 4) return fused_ta_stage_samples(variant - 4);
   return variant == 0 ? 128 : variant == 2 ? 64 : 96;
@@ -490,6 +491,9 @@ int fused_launches(int n_time) { return n_time <= 0 ? 0 : (n_time + kFusedWindow
 cudaError_t launch_xcorr_tc_fused_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                       int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
                                       cudaStream_t stream) {
+  if (variant == 10)  // the tensor-memory-A kernel's small-problem layout
+    return launch_xcorr_tc_fused_ta_ci4(in, row_chans, 3, n_time, n_chan, n_inputs, out, accumulate, status,
+                                        num_sms, stream);
   if (variant >= 7)
     return launch_xcorr_tc_fused_pair_ci4(in, row_chans, variant - 7, n_time, n_chan, n_inputs, out, accumulate,
                                           status, num_sms, stream);

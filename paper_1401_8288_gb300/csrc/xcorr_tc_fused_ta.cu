@@ -98,6 +98,11 @@ struct TParams {
   int n_kt;            // stages per tile pair
   int64_t n_pairs;
   int accumulate;      // add into out (else store)
+  // small-problem layout: pack_g channels of n_inputs each side by side in one tile (PACK), and
+  // each tile's stages cut into n_split items of split_kt stages whose results are added with
+  // atomics (atomic_out)
+  int pack_g, n_split, split_kt, atomic_out;
+  int n_items;         // items of a non-batch launch: tiles x n_split
   int2* out;
   int* status;
   uint32_t one;        // 1: a multiplier the compiler cannot fold (see lane_add)
@@ -114,10 +119,12 @@ struct TItem {
   int2* out;
   int64_t n_pairs;
   int c, I, J, n_inputs, n_kt, accumulate;
+  int t_first;             // first sample of the item
+  int ax, ay, bx, by;      // TMA coordinates (input or channel-input column, channel) of the row and column tiles
   bool diag, valid;
 };
 
-template <bool BATCH>
+template <bool BATCH, bool SMALL, bool PACK, int KT>
 __device__ __forceinline__ TItem resolve(const TParams& p, const CUtensorMap* map, int item, int n_items) {
   TItem it{};
   it.valid = item < n_items;
@@ -134,27 +141,49 @@ __device__ __forceinline__ TItem resolve(const TParams& p, const CUtensorMap* ma
     it.c = static_cast<int>(w.y);
     it.I = static_cast<int>(w.z);
     it.J = static_cast<int>(w.w);
+    it.t_first = 0;
   } else {
     it.map = map;
     it.out = p.out;
     it.n_pairs = p.n_pairs;
     it.n_inputs = p.n_inputs;
-    it.n_kt = p.n_kt;
     it.accumulate = p.accumulate;
-    it.c = item / p.n_tile_pairs;
-    tile_pair(item - it.c * p.n_tile_pairs, it.I, it.J);
+    int tile = item;
+    it.n_kt = p.n_kt;
+    it.t_first = p.t0;
+    if (SMALL) {  // the time split of the small-problem layout
+      tile = item / p.n_split;
+      const int split = item - tile * p.n_split;
+      it.n_kt = min(p.split_kt, p.n_kt - split * p.split_kt);
+      it.t_first = p.t0 + split * p.split_kt * KT;
+    }
+    if (PACK) {  // tile = a group of pack_g channels, one diagonal tile pair
+      it.c = tile;
+      it.I = it.J = 0;
+    } else {
+      it.c = tile / p.n_tile_pairs;
+      tile_pair(tile - it.c * p.n_tile_pairs, it.I, it.J);
+    }
   }
   it.diag = it.I == it.J;
+  if (PACK) {  // the packed view: x = channel * n_inputs + input over one time row
+    it.ax = it.bx = it.c * p.pack_g * p.n_inputs;
+    it.ay = it.by = 0;
+  } else {
+    it.ax = it.I * kBlk;
+    it.bx = it.J * kBlk;
+    it.ay = it.by = it.c;
+  }
   return it;
 }
 
-// L2 prefetch of stage s (KT samples from t0 + s KT) of an item: one box per tile.
+// L2 prefetch of stage s (KT samples from the item's first sample + s KT): one box per tile.
 template <int KT>
-__device__ __forceinline__ void prefetch_item_stage(const TItem& it, int t0, int s) {
+__device__ __forceinline__ void prefetch_item_stage(const TItem& it, int s) {
   if (!it.valid || s >= it.n_kt) return;
-  const int t = t0 + s * KT;
-  tma_prefetch_3d(it.map, it.I * kBlk, it.c, t);
-  if (!it.diag) tma_prefetch_3d(it.map, it.J * kBlk, it.c, t);
+  const int t = it.t_first + s * KT;
+  tma_prefetch_3d(it.map, it.ax, it.ay, t);
+  if (!it.diag) tma_prefetch_3d(it.map, it.bx, it.by, t);
 }
 
 // 16-byte chunk swizzle of the Re staging tile: a bijection of row % 8, so the eight rows of a
@@ -162,7 +191,7 @@ __device__ __forceinline__ void prefetch_item_stage(const TItem& it, int t0, int
 // of a phase-2 load) land in opposite halves of each eight-chunk group.
 __device__ __forceinline__ int staging_swizzle(int row) { return ((row & 1) << 2) | ((row >> 1) & 3); }
 
-template <int KT, int RAW, int DEC, bool BATCH>
+template <int KT, int RAW, int DEC, bool BATCH, bool SMALL, bool PACK>
 __global__ void __launch_bounds__(kThreads, 1)
     xcorr_tc_fused_ta_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ TParams p) {
   using G = TGeom<KT, RAW, DEC>;
@@ -212,37 +241,36 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int n_items = BATCH ? p.n_batch_items : p.n_chan * p.n_tile_pairs;
-  const int t0 = BATCH ? 0 : p.t0;
+  const int n_items = BATCH ? p.n_batch_items : p.n_items;
 
   if (warp == kProducerWarp) {
     if (lane == 0) {
       constexpr int kAhead = kPrefetchSamples / KT;  // L2 prefetch runs this many stages ahead of the loads
       if (!BATCH) prefetch_tmap(&raw_map);
-      TItem next = resolve<BATCH>(p, &raw_map, blockIdx.x, n_items);
+      TItem next = resolve<BATCH, SMALL, PACK, KT>(p, &raw_map, blockIdx.x, n_items);
       if (BATCH && next.valid) prefetch_tmap(next.map);
-      for (int s = 0; s < kAhead; ++s) prefetch_item_stage<KT>(next, t0, s);
+      for (int s = 0; s < kAhead; ++s) prefetch_item_stage<KT>(next, s);
       int r = 0;
       uint32_t ph = 0, filled = 0, fill_parity[RAW] = {};
       bool ok = true;
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
         const TItem it = next;
-        next = resolve<BATCH>(p, &raw_map, item + gridDim.x, n_items);
+        next = resolve<BATCH, SMALL, PACK, KT>(p, &raw_map, item + gridDim.x, n_items);
         if (BATCH && next.valid) prefetch_tmap(next.map);
         for (int tb = 0; tb < it.n_kt; ++tb) {
           if (tb + kAhead < it.n_kt)
-            prefetch_item_stage<KT>(it, t0, tb + kAhead);
+            prefetch_item_stage<KT>(it, tb + kAhead);
           else
-            prefetch_item_stage<KT>(next, t0, tb + kAhead - it.n_kt);
+            prefetch_item_stage<KT>(next, tb + kAhead - it.n_kt);
           if (!mbar_wait(&raw_empty[r], ph ^ 1u, abort_flag, p.status, DEV_TIMEOUT_EMPTY)) {
             ok = false;
             break;
           }
           uint8_t* st = raw + r * G::kRawStage;
-          const int t = t0 + tb * KT;
+          const int t = it.t_first + tb * KT;
           mbar_expect_tx(&raw_full[r], (it.diag ? 1 : 2) * G::kTile);
-          tma_load_3d(st, it.map, &raw_full[r], it.I * kBlk, it.c, t);
-          if (!it.diag) tma_load_3d(st + G::kTile, it.map, &raw_full[r], it.J * kBlk, it.c, t);
+          tma_load_3d(st, it.map, &raw_full[r], it.ax, it.ay, t);
+          if (!it.diag) tma_load_3d(st + G::kTile, it.map, &raw_full[r], it.bx, it.by, t);
           fill_parity[r] = ph;
           filled |= 1u << r;
           if (++r == RAW) {
@@ -268,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int r = 0, d = 0, g = 0;
     uint32_t rph = 0, dph = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
-      const TItem cur = resolve<BATCH>(p, &raw_map, item, n_items);
+      const TItem cur = resolve<BATCH, SMALL, PACK, KT>(p, &raw_map, item, n_items);
       // A sums: inputs 16 ib + lane / 4 (0) and + 8 (1), over samples 4 (lane % 4) .. + 3 of every 16
       uint32_t sar0 = 0u, sai0 = 0u, sar1 = 0u, sai1 = 0u;
       // B sums in 16-bit lanes: word e / 2, half e % 2 holds input e of chunk L
@@ -426,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const int n_kt = resolve<BATCH>(p, &raw_map, item, n_items).n_kt;
+        const int n_kt = resolve<BATCH, SMALL, PACK, KT>(p, &raw_map, item, n_items).n_kt;
         for (int tb = 0; tb < n_kt; ++tb) {
           if (!mbar_wait(&dec_full[d], dph, abort_flag, p.status, DEV_TIMEOUT_FULL)) {
             ok = false;
@@ -468,14 +496,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* tim = transpose + warp * 32 * kTPitch;
     int g = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
-      const TItem it = resolve<BATCH>(p, &raw_map, item, n_items);
+      const TItem it = resolve<BATCH, SMALL, PACK, KT>(p, &raw_map, item, n_items);
       const int c = it.c, I = it.I, J = it.J, n_inputs = it.n_inputs;
       const int t128 = 128 * it.n_kt * KT;  // 128 T over the padded block (padding decodes to u = 8 + 8i)
       const bool magic = t128 <= 128 * kMagicSamples;
       int2* out_c = it.out + (int64_t)c * it.n_pairs;
       const int row0 = I * kBlk + warp * 32;
       const int buf = g & 1;
-      if (it.accumulate) {
+      if (!SMALL && it.accumulate) {
         // the sums this tile pair adds to, pulled into L2 while its MMAs run: each thread
         // prefetches the 128-byte lines of its own row's segment (pairs J*128 .. min(J*128 + 127, i))
         const int i = I * kBlk + r_own;
@@ -491,8 +519,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           !mbar_wait_warp(&sfull[buf], (g >> 1) & 1, abort_flag, p.status, DEV_TIMEOUT_TMEM_FULL))
         break;
       tc_fence_after();
-      // 16-pair chunks this warp keeps: none past the inputs, none wholly above the diagonal
-      const int n_ch = row0 >= n_inputs ? 0 : I == J ? (warp * 32 + 31) / kChunk + 1 : kBlk / kChunk;
+      // 16-pair chunks this warp keeps: none past the inputs (the packed channels), none wholly
+      // above the diagonal
+      const int n_ch = (PACK ? (warp * 32 >= p.pack_g * n_inputs || c * p.pack_g + (warp * 32) / n_inputs >= p.n_chan)
+                             : row0 >= n_inputs)
+                           ? 0
+                       : I == J ? (warp * 32 + 31) / kChunk + 1
+                                : kBlk / kChunk;
       {
         uint4* srow = reinterpret_cast<uint4*>(staging + r_own * kBlk);
         const int sw = staging_swizzle(r_own);
@@ -533,9 +566,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
 #pragma unroll
         for (int rw = 0; rw < 4; ++rw) {
-          const int rl = 8 * rw + rg, rr = warp * 32 + rl, i = I * kBlk + rr;
+          const int rl = 8 * rw + rg, rr = warp * 32 + rl;
+          int i, first = 0;  // the row's input, and its first column in the tile
+          int2* row_out;     // the row's pairs (j = first .. last of the tile)
+          if (PACK) {
+            const int blk = rr / n_inputs, cr = c * p.pack_g + blk;
+            if (blk >= p.pack_g || cr >= p.n_chan) continue;
+            first = blk * n_inputs;
+            i = rr - first;
+            row_out = it.out + (int64_t)cr * it.n_pairs + (int64_t)i * (i + 1) / 2;
+          } else {
+            i = I * kBlk + rr;
+            if (i >= n_inputs) continue;
+            row_out = out_c + (int64_t)i * (i + 1) / 2 + J * kBlk;
+          }
           const int last = I == J ? rr : kBlk - 1;  // last column of the row in the tile
-          if (i >= n_inputs || jl0 > last) continue;
+          // (first is a multiple of 16 and jl0 of 4: a run of four starts inside the row or wholly before it)
+          if (jl0 > last || jl0 < first) continue;
           const uint4 re4 =
               *reinterpret_cast<const uint4*>(staging + rr * kBlk + (((jl0 >> 2) ^ staging_swizzle(rr)) << 2));
           const uint4 im4 = *reinterpret_cast<const uint4*>(tim + rl * kTPitch + 4 * q4);
@@ -555,9 +602,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             v[k] = make_int2(nr + rc.x - sp[k], -ni + rc.y + sq[k]);
           }
-          int2* dst = out_c + (int64_t)i * (i + 1) / 2 + J * kBlk + jl0;
+          int2* dst = row_out + (jl0 - first);
           const int nv = last - jl0 + 1 < 4 ? last - jl0 + 1 : 4;
-          if (nv == 4 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+          if (SMALL && p.atomic_out) {  // time-split items of one tile add into the same pairs
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if (k < nv) {
+                atomicAdd(&dst[k].x, v[k].x);
+                atomicAdd(&dst[k].y, v[k].y);
+              }
+            }
+          } else if (nv == 4 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
             int4* d4 = reinterpret_cast<int4*>(dst);
             int4 w0 = make_int4(v[0].x, v[0].y, v[1].x, v[1].y), w1 = make_int4(v[2].x, v[2].y, v[3].x, v[3].y);
             if (it.accumulate) {
@@ -598,10 +653,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int KT, int RAW, int DEC, bool BATCH = false>
+template <int KT, int RAW, int DEC, bool BATCH = false, bool SMALL = false, bool PACK = false>
 cudaError_t launch_ta(const CUtensorMap& raw_map, const TParams& p, int grid, cudaStream_t stream) {
   using G = TGeom<KT, RAW, DEC>;
-  auto kern = xcorr_tc_fused_ta_kernel<KT, RAW, DEC, BATCH>;
+  auto kern = xcorr_tc_fused_ta_kernel<KT, RAW, DEC, BATCH, SMALL, PACK>;
   static int attr_device = -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -617,8 +672,22 @@ cudaError_t launch_ta(const CUtensorMap& raw_map, const TParams& p, int grid, cu
 
 }  // namespace
 
-// The tensor-memory-A shapes: 128 samples with 2 raw + 2 decoded stages, 96 with 3 + 2, 64 with 4 + 4.
-int fused_ta_stage_samples(int variant) { return variant == 0 ? 128 : variant == 1 ? 96 : 64; }
+// The tensor-memory-A shapes: 128 samples with 2 raw + 2 decoded stages, 96 with 3 + 2, 64 with 4 + 4,
+// and (3) the small-problem layout on 128 x (2 + 2).
+int fused_ta_stage_samples(int variant) { return variant == 0 || variant == 3 ? 128 : variant == 1 ? 96 : 64; }
+
+// The small-problem layout of a launch: channels packed per tile and the time split.
+void small_layout(int n_chan, int n_inputs, int n_kt, int num_sms, int& pack_g, int& tiles, int& n_split,
+                  int& split_kt) {
+  const int nb = (n_inputs + kBlk - 1) / kBlk;
+  pack_g = n_inputs <= kBlk / 2 ? kBlk / n_inputs : 1;
+  tiles = pack_g > 1 ? (n_chan + pack_g - 1) / pack_g : n_chan * (nb * (nb + 1) / 2);
+  // as many splits as keep the items within one wave of the SMs, each at least one stage long
+  n_split = tiles >= num_sms ? 1 : num_sms / tiles;
+  if (n_split > n_kt) n_split = n_kt;
+  split_kt = (n_kt + n_split - 1) / n_split;
+  n_split = (n_kt + split_kt - 1) / split_kt;
+}
 
 cudaError_t launch_xcorr_tc_fused_ta_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                          int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
@@ -636,22 +705,48 @@ cudaError_t launch_xcorr_tc_fused_ta_ci4(const uint8_t* in, int row_chans, int v
   p.out = out;
   p.status = status;
   p.one = 1u;
-  const int64_t items = (int64_t)n_chan * p.n_tile_pairs;
-  const int grid = static_cast<int>(items < num_sms ? items : num_sms);
+  const bool small = variant == 3;
   CUtensorMap raw_map;
-  if (row_chans < n_chan || !encode_raw_ci4_tmap(&raw_map, in, n_inputs, n_chan, row_chans, n_time, kt, nullptr))
+  if (row_chans < n_chan) return cudaErrorInvalidValue;
+  int pack_g = 1;
+  if (small) pack_g = n_inputs <= kBlk / 2 ? kBlk / n_inputs : 1;
+  if (pack_g > 1) {
+    // the packed view: one time row is n_chan * n_inputs bytes (channel-major), read in boxes of 128
+    // (pack_g channels side by side) x 1 x kt; the middle dimension has extent 1
+    if (!encode_raw_ci4_packed_tmap(&raw_map, in, n_inputs, n_chan, row_chans, n_time, kt, nullptr))
+      return cudaErrorInvalidValue;
+  } else if (!encode_raw_ci4_tmap(&raw_map, in, n_inputs, n_chan, row_chans, n_time, kt, nullptr)) {
     return cudaErrorInvalidValue;
+  }
+  p.pack_g = pack_g;
   // one exactly-summed block per launch; later blocks add into the first
   for (int t0 = 0; t0 < n_time; t0 += kFusedWindowCI4) {
     const int len = n_time - t0 < kFusedWindowCI4 ? n_time - t0 : kFusedWindowCI4;
     p.t0 = t0;
     p.n_kt = (len + kt - 1) / kt;
     p.accumulate = (accumulate || t0 > 0) ? 1 : 0;
+    int tiles = n_chan * p.n_tile_pairs;
+    p.n_split = 1;
+    p.split_kt = p.n_kt;
+    if (small) small_layout(n_chan, n_inputs, p.n_kt, num_sms, pack_g, tiles, p.n_split, p.split_kt);
+    p.atomic_out = p.n_split > 1 ? 1 : 0;
+    p.n_items = tiles * p.n_split;
+    if (p.atomic_out && !p.accumulate) {  // the split items add into a cleared output
+      cudaError_t e = cudaMemsetAsync(out, 0, (size_t)n_chan * p.n_pairs * sizeof(int2), stream);
+      if (e != cudaSuccess) return e;
+      p.accumulate = 1;
+    }
+    const int grid = p.n_items < num_sms ? p.n_items : num_sms;
     cudaError_t e;
     switch (variant) {
       case 0: e = launch_ta<128, 2, 2>(raw_map, p, grid, stream); break;
       case 1: e = launch_ta<96, 3, 2>(raw_map, p, grid, stream); break;
-      default: e = launch_ta<64, 4, 4>(raw_map, p, grid, stream); break;
+      case 2: e = launch_ta<64, 4, 4>(raw_map, p, grid, stream); break;
+      default:  // the small-problem layout; with neither packing nor a split it is shape 0's launch
+        e = pack_g > 1         ? launch_ta<128, 2, 2, false, true, true>(raw_map, p, grid, stream)
+            : p.n_split > 1    ? launch_ta<128, 2, 2, false, true, false>(raw_map, p, grid, stream)
+                               : launch_ta<128, 2, 2>(raw_map, p, grid, stream);
+        break;
     }
     if (e != cudaSuccess) return e;
   }
@@ -671,6 +766,7 @@ cudaError_t launch_xcorr_tc_fused_ta_batch(const TaSubDesc* subs, const uint4* i
   TParams p{};
   p.status = status;
   p.one = 1u;
+  p.n_split = 1;
   p.subs = subs;
   p.items = items;
   p.n_batch_items = n_items;

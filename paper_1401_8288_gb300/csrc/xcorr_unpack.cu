@@ -142,8 +142,51 @@ bool encode_plane_tmap(CUtensorMap* map, void* planes, int elem_bytes, int n_inp
   return true;
 }
 
+namespace {
+// The raw-input maps are pure functions of their arguments and are rebuilt by every execute;
+// the last few are kept per host thread, so that an execute that repeats an earlier one (the
+// usual case: the same buffer every integration) skips the driver's encode.
+struct RawMapMemo {
+  const void* in = nullptr;
+  int n_inputs = 0, n_chan = 0, row_chans = 0, n_time = 0, box_t = 0, box_i = 0, packed = -1;
+  CUtensorMap map;
+};
+constexpr int kRawMapMemo = 4;
+thread_local RawMapMemo t_raw_memo[kRawMapMemo];
+thread_local int t_raw_memo_next = 0;
+
+RawMapMemo* raw_memo_find(const void* in, int n_inputs, int n_chan, int row_chans, int n_time, int box_t, int box_i,
+                          int packed) {
+  for (RawMapMemo& m : t_raw_memo)
+    if (m.packed == packed && m.in == in && m.n_inputs == n_inputs && m.n_chan == n_chan &&
+        m.row_chans == row_chans && m.n_time == n_time && m.box_t == box_t && m.box_i == box_i)
+      return &m;
+  return nullptr;
+}
+
+void raw_memo_put(const CUtensorMap& map, const void* in, int n_inputs, int n_chan, int row_chans, int n_time,
+                  int box_t, int box_i, int packed) {
+  RawMapMemo& m = t_raw_memo[t_raw_memo_next];
+  t_raw_memo_next = (t_raw_memo_next + 1) % kRawMapMemo;
+  m.in = in;
+  m.n_inputs = n_inputs;
+  m.n_chan = n_chan;
+  m.row_chans = row_chans;
+  m.n_time = n_time;
+  m.box_t = box_t;
+  m.box_i = box_i;
+  m.packed = packed;
+  m.map = map;
+}
+
+}  // namespace
+
 bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int row_chans, int n_time,
                          int box_t, std::string* err, int box_i) {
+  if (const RawMapMemo* m = raw_memo_find(in, n_inputs, n_chan, row_chans, n_time, box_t, box_i, 0)) {
+    *map = m->map;
+    return true;
+  }
   auto fn = encode_tiled_fn(err);
   if (!fn) return false;
   std::memset(map, 0, sizeof(*map));
@@ -165,6 +208,35 @@ bool encode_raw_ci4_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_c
     if (err) *err = "cuTensorMapEncodeTiled (raw input) failed with CUresult " + std::to_string((int)r);
     return false;
   }
+  raw_memo_put(*map, in, n_inputs, n_chan, row_chans, n_time, box_t, box_i, 0);
+  return true;
+}
+
+bool encode_raw_ci4_packed_tmap(CUtensorMap* map, const void* in, int n_inputs, int n_chan, int row_chans,
+                                int n_time, int box_t, std::string* err) {
+  if (const RawMapMemo* m = raw_memo_find(in, n_inputs, n_chan, row_chans, n_time, box_t, 128, 1)) {
+    *map = m->map;
+    return true;
+  }
+  auto fn = encode_tiled_fn(err);
+  if (!fn) return false;
+  std::memset(map, 0, sizeof(*map));
+  // the caller's [t][c][i] bytes with channel and input merged into one dimension of n_chan *
+  // n_inputs bytes (dim0), an extent-1 dimension (dim1, so that the kernels' 3-D loads serve),
+  // and time (dim2); a box is box_t rows of 128 bytes, consecutive channels side by side
+  const cuuint64_t row = (cuuint64_t)n_inputs * (cuuint64_t)row_chans;
+  cuuint64_t dims[3] = {(cuuint64_t)n_inputs * (cuuint64_t)n_chan, 1, (cuuint64_t)n_time};
+  cuuint64_t strides[2] = {row, row};
+  cuuint32_t box[3] = {128, 1, (cuuint32_t)box_t};
+  cuuint32_t elem_strides[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(in), dims, strides, box, elem_strides,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (err) *err = "cuTensorMapEncodeTiled (packed raw input) failed with CUresult " + std::to_string((int)r);
+    return false;
+  }
+  raw_memo_put(*map, in, n_inputs, n_chan, row_chans, n_time, box_t, 128, 1);
   return true;
 }
 

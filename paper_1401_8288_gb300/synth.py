@@ -162,18 +162,21 @@ def quarter_turn_tone_ci4(n_time: int, n_chan: int, n_sta: int, seed: int,
     return np.broadcast_to(packed, (n_time, n_chan, n_sta, 2)).copy(), q
 
 
-def subarray_batch(seed: int, count: int = 24) -> list[dict]:
+def subarray_batch(seed: int, count: int = 24, inputs=(16, 704), channels=(64, 1024),
+                   samples=(512, 8192)) -> list[dict]:
     """Sizes of a batch of independent correlations of uneven size.
 
-    Input counts from {16, 32, ..., 704}, channel counts from {64, 128, ...,
-    1024}, integration lengths from {512, 1024, ..., 8192}; the input count is
-    even (two polarisations per station).  Each entry also carries its own
-    sample seed.
+    Input counts uniform over the multiples of 16 in ``inputs`` (default
+    {16, 32, ..., 704}), channel counts over the multiples of the lower bound
+    in ``channels`` (default {64, 128, ..., 1024}), integration lengths over
+    the multiples of the lower bound in ``samples`` (default {512, ..., 8192});
+    the input count is even (two polarisations per station).  Each entry also
+    carries its own sample seed.
     """
     rng = _rng(seed)
-    ni = rng.integers(1, 45, size=count) * 16
-    nc = rng.integers(1, 17, size=count) * 64
-    nt = rng.integers(1, 17, size=count) * 512
+    ni = rng.integers(inputs[0] // 16, inputs[1] // 16 + 1, size=count) * 16
+    nc = rng.integers(1, channels[1] // channels[0] + 1, size=count) * channels[0]
+    nt = rng.integers(1, samples[1] // samples[0] + 1, size=count) * samples[0]
     seeds = rng.integers(0, 2**31 - 1, size=count)
     return [dict(n_inputs=int(a), n_sta=int(a) // 2, n_chan=int(b), n_time=int(c),
                  seed=int(s)) for a, b, c, s in zip(ni, nc, nt, seeds)]

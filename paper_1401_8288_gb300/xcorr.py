@@ -38,7 +38,9 @@ EXPORTS = ("xcorr_plan_create", "xcorr_execute", "xcorr_dump", "xcorr_sync", "xc
            "xcorr_stream_commit", "xcorr_stream_flush", "xcorr_stream_counters",
            "xcorr_stream_wait_dump", "xcorr_stream_destroy", "xcorr_packets_advance",
            "xcorr_execute_dump_host", "xcorr_bdi_create", "xcorr_bdi_step", "xcorr_bdi_destroy",
-           "xcorr_watchdog_selftest")
+           "xcorr_watchdog_selftest", "xcorr_autotune_cached", "xcorr_tuning_cache_load",
+           "xcorr_tuning_cache_save", "xcorr_tuning_cache_clear", "xcorr_batch_set_subarray_variants",
+           "xcorr_batch_get_subarray_variants", "xcorr_batch_autotune")
 XCORR_PACKET_HEADER_BYTES = 16
 XCORR_EVENT_OPEN, XCORR_EVENT_CLOSE = 1, 2
 PEAK_KINDS = {"tc_e4m3": 0, "tc_bf16": 1, "mma_sync_s8": 2, "dp4a": 3}
@@ -136,6 +138,14 @@ def load():
                 "xcorr_batch_destroy": [vp],
                 "xcorr_autotune": [vp, vp, i, vp, ctypes.POINTER(xcorr_tuning),
                                    ctypes.POINTER(ctypes.c_float)],
+                "xcorr_autotune_cached": [vp, vp, i, vp, ctypes.POINTER(xcorr_tuning),
+                                          ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i)],
+                "xcorr_tuning_cache_load": [ctypes.c_char_p, ctypes.POINTER(i), ctypes.POINTER(i)],
+                "xcorr_tuning_cache_save": [ctypes.c_char_p, ctypes.POINTER(i)],
+                "xcorr_tuning_cache_clear": [],
+                "xcorr_batch_set_subarray_variants": [vp, ctypes.POINTER(i)],
+                "xcorr_batch_get_subarray_variants": [vp, ctypes.POINTER(i)],
+                "xcorr_batch_autotune": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.POINTER(i)],
                 "xcorr_tracker_create": [ctypes.POINTER(vp), ctypes.POINTER(xcorr_stream_config), i,
                                          i],
                 "xcorr_tracker_feed": [vp, vp, i64, i64, vp, ctypes.POINTER(xcorr_block_event), i,
@@ -247,6 +257,32 @@ def xcorr_autotune(plan, d_in: int, n_time: int, stream: int = 0) -> tuple[dict,
     return _tuning_dict(t), ms.value
 
 
+def xcorr_autotune_cached(plan, d_in: int, n_time: int, stream: int = 0) -> tuple[dict, float, bool]:
+    """xcorr_autotune through the process's tuning cache: (shape, ms, taken from the cache)."""
+    t, ms, hit = xcorr_tuning(), ctypes.c_float(), ctypes.c_int()
+    _check(load().xcorr_autotune_cached(plan, d_in, n_time, stream, ctypes.byref(t), ctypes.byref(ms),
+                                        ctypes.byref(hit)))
+    return _tuning_dict(t), ms.value, bool(hit.value)
+
+
+def xcorr_tuning_cache_load(path: str) -> tuple[int, int]:
+    """Merge a JSON-lines tuning file into the process's cache: (entries loaded, lines skipped)."""
+    n, bad = ctypes.c_int(), ctypes.c_int()
+    _check(load().xcorr_tuning_cache_load(os.fsencode(path), ctypes.byref(n), ctypes.byref(bad)))
+    return n.value, bad.value
+
+
+def xcorr_tuning_cache_save(path: str) -> int:
+    """Write the process's tuning cache to a JSON-lines file; returns the entry count."""
+    n = ctypes.c_int()
+    _check(load().xcorr_tuning_cache_save(os.fsencode(path), ctypes.byref(n)))
+    return n.value
+
+
+def xcorr_tuning_cache_clear() -> None:
+    _check(load().xcorr_tuning_cache_clear())
+
+
 def xcorr_destroy(plan) -> None:
     _check(load().xcorr_destroy(plan))
 
@@ -304,6 +340,22 @@ def xcorr_batch_create(subarrays: list[tuple[int, int, int]]) -> ctypes.c_void_p
 
 def xcorr_batch_set_variant(batch, stage_variant: int) -> None:
     _check(load().xcorr_batch_set_variant(batch, stage_variant))
+
+
+def xcorr_batch_set_subarray_variants(batch, variants: list[int]) -> None:
+    _check(load().xcorr_batch_set_subarray_variants(batch, (ctypes.c_int * len(variants))(*variants)))
+
+
+def xcorr_batch_get_subarray_variants(batch, n: int) -> list[int]:
+    v = (ctypes.c_int * n)()
+    _check(load().xcorr_batch_get_subarray_variants(batch, v))
+    return list(v)
+
+
+def xcorr_batch_autotune(batch, d_ins: list[int], d_outs: list[int], stream: int = 0) -> list[int]:
+    v = (ctypes.c_int * len(d_ins))()
+    _check(load().xcorr_batch_autotune(batch, _ptrs(d_ins), _ptrs(d_outs), stream, v))
+    return list(v)
 
 
 def xcorr_batch_execute(batch, d_ins: list[int], d_outs: list[int], stream: int = 0) -> None:
@@ -552,6 +604,18 @@ class Batch:
     def set_variant(self, stage_variant: int) -> None:
         xcorr_batch_set_variant(self.handle, stage_variant)
 
+    def set_subarray_variants(self, variants: list[int]) -> None:
+        xcorr_batch_set_subarray_variants(self.handle, list(variants))
+
+    def subarray_variants(self) -> list[int]:
+        return xcorr_batch_get_subarray_variants(self.handle, len(self.subarrays))
+
+    def autotune(self, inputs, stream=None) -> list[int]:
+        """Per subarray, the fused shape that runs it fastest (or the cached one);
+        overwrites the outputs."""
+        return xcorr_batch_autotune(self.handle, [x.data_ptr() for x in inputs],
+                                    [o.data_ptr() for o in self.outputs], self._stream(stream))
+
     def execute(self, inputs, stream=None):
         xcorr_batch_execute(self.handle, [x.data_ptr() for x in inputs],
                             [o.data_ptr() for o in self.outputs], self._stream(stream))
@@ -612,7 +676,11 @@ class Plan:
                    unfused: int = 0) -> None:
         xcorr_plan_set_tuning(self.handle, stage_variant, groups, x_streams, unfused)
 
-    def autotune(self, x, stream=None) -> tuple[dict, float]:
+    def autotune(self, x, stream=None, cached: bool = False):
+        """Time every launch shape on x and keep the fastest: (shape, ms); with
+        cached=True through the process's tuning cache: (shape, ms, from_cache)."""
+        if cached:
+            return xcorr_autotune_cached(self.handle, x.data_ptr(), x.shape[0], self._stream(stream))
         return xcorr_autotune(self.handle, x.data_ptr(), x.shape[0], self._stream(stream))
 
     def _stream(self, stream) -> int:

@@ -96,3 +96,32 @@ def test_baseline_index_matches_the_packed_triangle(lib):
     assert all(len(v) == 1 or (v[0][0] == v[0][1]) for v in seen.values())
     with pytest.raises(xcorr.XcorrError):
         xcorr.xcorr_baseline_index(ns, 1, 2, 0, 0)  # b > a
+
+
+def test_tuning_cache_file_round_trip(lib, tmp_path):
+    # the autotuners' cache in JSON lines: every field read back, unreadable lines skipped
+    import json
+    good = {"scope": "plan", "device": "NVIDIA GB300", "sms": 152, "fmt": 0, "n_inputs": 512,
+            "n_channels": 512, "n_time": 2048, "stage_variant": 4, "groups": 1, "x_streams": 1,
+            "unfused": 0, "us": 501}
+    batch = dict(good, scope="batch", n_inputs=64, n_channels=64, n_time=1024, stage_variant=3, us=12)
+    path = tmp_path / "tuning.jsonl"
+    lines = [json.dumps(good), "not json at all", json.dumps(dict(good, stage_variant=99)),
+             json.dumps({k: v for k, v in good.items() if k != "groups"}), json.dumps(batch), ""]
+    path.write_text("\n".join(lines) + "\n")
+    xcorr.xcorr_tuning_cache_clear()
+    assert xcorr.xcorr_tuning_cache_load(str(path)) == (2, 3)
+    out = tmp_path / "saved.jsonl"
+    assert xcorr.xcorr_tuning_cache_save(str(out)) == 2
+    saved = [json.loads(line) for line in out.read_text().splitlines()]
+    assert sorted(saved, key=lambda d: d["scope"]) == [batch, good]
+    # the same problem loaded again replaces its entry; clear empties the cache
+    path.write_text(json.dumps(dict(good, stage_variant=8, us=512)) + "\n")
+    assert xcorr.xcorr_tuning_cache_load(str(path)) == (1, 0)
+    assert xcorr.xcorr_tuning_cache_save(str(out)) == 2
+    assert {d["scope"]: d["stage_variant"] for d in map(json.loads, out.read_text().splitlines())} == \
+        {"plan": 8, "batch": 3}
+    xcorr.xcorr_tuning_cache_clear()
+    assert xcorr.xcorr_tuning_cache_save(str(out)) == 0
+    with pytest.raises(xcorr.XcorrError):
+        xcorr.xcorr_tuning_cache_load(str(tmp_path / "missing.jsonl"))

@@ -248,6 +248,25 @@ def test_budget_and_query(torch):
         assert info["output_bytes"] == 64 * 131328 * 8
 
 
+def test_auto_engine_and_default_shape_follow_the_measured_rule(torch):
+    # AUTO: CUDA-core only for integer input below 16 inputs and at most 16 channels
+    cases = [((4, 8, 1024, "ci4"), xcorr.XCORR_ENGINE_CUDA_CORE), ((4, 16, 256, "ci8"), xcorr.XCORR_ENGINE_CUDA_CORE),
+             ((8, 8, 1024, "ci4"), xcorr.XCORR_ENGINE_TENSOR), ((4, 17, 64, "ci4"), xcorr.XCORR_ENGINE_TENSOR),
+             ((2, 4, 64, "cf32"), xcorr.XCORR_ENGINE_TENSOR)]
+    for (ns, nc, nt, fmt), engine in cases:
+        with xcorr.Plan(ns, nc, nt, fmt=fmt, engine="auto") as plan:
+            assert plan.query()["engine"] == engine, (ns, nc, nt, fmt)
+    # a 4-bit plan's first shape: the small-problem layout for N_i <= 64 with K >= 1024 or C >= 256
+    for (ns, nc, nt), shape in [((32, 64, 1024), 10), ((8, 256, 256), 10), ((32, 64, 256), 4),
+                                ((256, 64, 2048), 4), ((40, 64, 2048), 4)]:
+        with xcorr.Plan(ns, nc, nt, engine="tensor") as plan:
+            assert plan.query()["tuning"]["stage_variant"] == shape, (ns, nc, nt)
+    # and the answers stay the oracle's on the CUDA-core side of the rule
+    x = synth.uniform_ci4(1024, 8, 4, seed=81, lo=-8, hi=7)
+    got, _ = run(torch, x, "auto")
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
 # -------------------------------------------------- int8 on tensor cores ---
 
 @pytest.mark.parametrize("n_sta,n_chan,n_time", [(1, 2, 7), (37, 3, 150), (70, 2, 1000), (136, 2, 385)])
@@ -328,7 +347,7 @@ def test_every_launch_shape_is_exact(torch, variant, groups, x_streams):
     assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("n_sta,n_chan,n_time", [(8, 1, 1), (8, 2, 65), (64, 3, 300), (72, 2, 257),
                                                  (200, 2, 385), (256, 3, 1000)])
 def test_fused_4bit_kernel_bit_exact(torch, variant, n_sta, n_chan, n_time):
@@ -373,7 +392,7 @@ def test_pair_kernel_accumulates_over_executes(torch, n_sta):
 FUSED_BLOCK = 37248  # samples per exactly-summed block of the fused kernel
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("pattern", ["max", "extremes"])
 def test_fused_exact_across_blocks_at_the_bound(torch, variant, pattern):
     # Two full blocks and a tail.  "max": every sample 7 + 7i, so each block's
@@ -392,6 +411,69 @@ def test_fused_exact_across_blocks_at_the_bound(torch, variant, pattern):
     if pattern == "max":
         assert (want[..., 0] == 98 * n_time).all() and (want[..., 1] == 0).all()
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n_sta,n_chan,n_time", [
+    (8, 37, 1000),   # 16 inputs: 8 channels per tile, a ragged last group of 5
+    (16, 9, 640),    # 32 inputs: 4 per tile
+    (24, 7, 513),    # 48 inputs: 2 per tile (rows 96-127 of each tile unused), a ragged stage
+    (32, 64, 1024),  # 64 inputs: 2 per tile, the small field-system-sized workload
+    (32, 3, 4096),   # few tiles: 32 stages split over the SMs
+    (100, 2, 1100),  # 200 inputs: no packing, 3 tile pairs per channel, time split
+])
+def test_small_problem_layout_bit_exact(torch, n_sta, n_chan, n_time):
+    # Shape 10: channels packed side by side into one 128-row tile (N_i <= 64) and each
+    # tile's stages split over the SMs, the split items adding their sums atomically
+    x = synth.uniform_ci4(n_time, n_chan, n_sta, seed=n_sta * 31 + n_chan, lo=-8, hi=7)
+    got, _ = run(torch, x, "tensor", tuning=(10, 0, 2, 0))
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+
+
+def test_small_problem_layout_over_several_executes_and_execute_dump(torch):
+    chunks = [300, 128, 77]
+    x = synth.uniform_ci4(sum(chunks), 10, 16, seed=91, lo=-8, hi=7)
+    got, n = run(torch, x, "tensor", chunks=chunks, tuning=(10, 0, 2, 0))
+    assert n == sum(chunks)
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+    # execute_dump into the caller's buffer: split items clear it first, every call
+    y = synth.uniform_ci4(512, 10, 16, seed=92, lo=-8, hi=7)
+    yd = torch.from_numpy(y).cuda()
+    with xcorr.Plan(16, 10, 512) as plan:
+        plan.set_tuning(10, 0, 2, 0)
+        out = torch.full((10, plan.info["n_pairs"], 2), 99, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            plan.execute_dump(yd, out)
+        plan.sync()
+    assert np.array_equal(out.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, y))
+
+
+@pytest.mark.parametrize("engine,tuning", [("tensor", (4, 0, 2, 0)), ("tensor", (10, 0, 2, 0)),
+                                           ("cuda_core", None)])
+def test_execute_dump_replayed_from_a_cuda_graph(torch, engine, tuning):
+    # one execute_dump recorded in a CUDA graph (the way small problems are driven without a
+    # host call per integration); replays read the input buffer in place
+    sizes = (32, 12, 512)  # 64 inputs, 12 channels: packed in the small layout, time split
+    x, y = (synth.uniform_ci4(sizes[2], sizes[1], sizes[0], seed=s, lo=-8, hi=7) for s in (61, 62))
+    xd = torch.from_numpy(x).cuda()
+    with xcorr.Plan(sizes[0], sizes[1], sizes[2], engine=engine) as plan:
+        if tuning is not None:
+            plan.set_tuning(*tuning)
+        out = torch.zeros((sizes[1], plan.info["n_pairs"], 2), dtype=torch.int32, device="cuda")
+        plan.execute_dump(xd, out)  # warm-up outside the capture
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            plan.execute_dump(xd, out)
+        out.fill_(-1)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, x))
+        xd.copy_(torch.from_numpy(y).cuda())
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, y))
+        plan.sync()
 
 
 def test_fused_falls_back_for_unaligned_input(torch):
@@ -420,7 +502,7 @@ def test_autotune_keeps_results_exact(torch):
     with xcorr.Plan(128, 64, 256) as plan:
         plan.execute(xd)  # an integration in progress is discarded by the autotuner
         best, ms = plan.autotune(xd)
-        assert 0 <= best["stage_variant"] <= 9 and 1 <= best["groups"] <= 8 and ms > 0
+        assert 0 <= best["stage_variant"] <= 10 and 1 <= best["groups"] <= 8 and ms > 0
         assert plan.query()["samples_integrated"] == 0
         assert plan.query()["tuning"]["stage_variant"] == best["stage_variant"]
         plan.execute(xd)
@@ -502,11 +584,85 @@ def test_fused_batch_is_the_default_and_replays_new_data(torch):
             assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, y))
 
 
+def test_batch_a_shape_per_subarray(torch):
+    # shared classes of the tensor-memory-A shapes (4, 5, 6) and subarrays launched alone (the
+    # CTA-pair kernel 8, the small-problem layout 10, the shared-memory kernel 1), all on their
+    # own streams, in an execute and in a graph
+    variants = [4, 5, 6, 8, 10, 1]
+    xs, ys = batch_inputs(FUSABLE, 500), batch_inputs(FUSABLE, 501)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    with xcorr.Batch(FUSABLE) as batch:
+        batch.set_subarray_variants(variants)
+        assert batch.subarray_variants() == variants
+        outs = batch.execute(xd)
+        batch.sync()
+        for x, o in zip(xs, outs):
+            assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, x))
+        batch.capture(xd)
+        for dst, y in zip(xd, ys):
+            dst.copy_(torch.from_numpy(y).cuda())
+        outs = batch.replay()
+        batch.sync()
+        for y, o in zip(ys, outs):
+            assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, y))
+        with pytest.raises(xcorr.XcorrError):
+            batch.set_subarray_variants([4, 4, 4, 11, 4, 4])  # 11 is no plan shape
+        batch.set_variant(4)  # batch-wide shape 4: plan shape 5 for every subarray
+        assert batch.subarray_variants() == [5] * len(FUSABLE)
+
+
+def test_batch_autotune_per_subarray_and_its_cache(torch, tmp_path):
+    import json
+    sizes = FUSABLE[:3]
+    xs = batch_inputs(sizes, 600)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    xcorr.xcorr_tuning_cache_clear()
+    with xcorr.Batch(sizes) as batch:
+        picked = batch.autotune(xd)
+        assert all(0 <= v <= 10 for v in picked) and batch.subarray_variants() == picked
+        outs = batch.execute(xd)
+        batch.sync()
+        for x, o in zip(xs, outs):
+            assert np.array_equal(o.cpu().numpy().astype(np.int64), oracle.correlate(oracle.FMT_CI4, x))
+    path = tmp_path / "tuning.jsonl"
+    assert xcorr.xcorr_tuning_cache_save(str(path)) == 3
+    entries = [json.loads(line) for line in path.read_text().splitlines()]
+    assert {(e["n_inputs"], e["n_channels"], e["n_time"]) for e in entries} == \
+        {(2 * ns, nc, nt) for ns, nc, nt in sizes}
+    assert all(e["scope"] == "batch" for e in entries)
+    # a fresh process state with the file loaded: the same shapes without timing
+    xcorr.xcorr_tuning_cache_clear()
+    assert xcorr.xcorr_tuning_cache_load(str(path)) == (3, 0)
+    with xcorr.Batch(sizes) as batch:
+        assert batch.autotune(xd) == picked
+    xcorr.xcorr_tuning_cache_clear()
+
+
+def test_plan_autotune_through_the_cache(torch):
+    x = synth.uniform_ci4(256, 8, 32, seed=71, lo=-8, hi=7)
+    xd = torch.from_numpy(x).cuda()
+    xcorr.xcorr_tuning_cache_clear()
+    with xcorr.Plan(32, 8, 256) as plan:
+        best, ms, hit = plan.autotune(xd, cached=True)
+        assert not hit and ms > 0
+    with xcorr.Plan(32, 8, 256) as plan:
+        best2, ms2, hit2 = plan.autotune(xd, cached=True)
+        assert hit2 and best2 == best and ms2 == pytest.approx(ms, abs=1e-3)
+        plan.execute(xd)
+        got = plan.dump().cpu().numpy()
+        plan.sync()
+    assert np.array_equal(got.astype(np.int64), oracle.correlate(oracle.FMT_CI4, x))
+    xcorr.xcorr_tuning_cache_clear()
+
+
 def test_fused_shapes_refused_for_batches_they_do_not_fit(torch):
     with xcorr.Batch([(70, 2, 200)]) as batch:  # 140 inputs: not a multiple of 16
         with pytest.raises(xcorr.XcorrError) as e:
             batch.set_variant(3)
         assert e.value.status == 2  # UNSUPPORTED
+        with pytest.raises(xcorr.XcorrError) as e:
+            batch.set_subarray_variants([4])
+        assert e.value.status == 2
         batch.set_variant(0)
 
 
@@ -551,6 +707,7 @@ def workload_512():
     ("tensor", (0, 0, 2, 0)), ("tensor", (3, 0, 2, 0)),
     ("tensor", (4, 0, 2, 0)), ("tensor", (5, 0, 2, 0)), ("tensor", (6, 0, 2, 0)),  # A in tensor memory
     ("tensor", (7, 0, 2, 0)), ("tensor", (8, 0, 2, 0)), ("tensor", (9, 0, 2, 0)),  # CTA pairs
+    ("tensor", (10, 0, 2, 0)),  # the small-problem layout (at this size: neither packed nor split)
     ("tensor", (0, 1, 1, 1)),   # the planes path
     ("cuda_core", None)])
 def test_workload_512_inputs_512_channels_2048_samples(torch, workload_512, engine, tuning):
