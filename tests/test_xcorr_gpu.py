@@ -716,7 +716,7 @@ def test_workload_512_inputs_512_channels_2048_samples(torch, workload_512, engi
                  seed=3)
 
 
-@pytest.mark.parametrize("variant", [4, 8])
+@pytest.mark.parametrize("variant", [4, 8, 10])
 def test_workload_512_execute_dump_into_the_callers_buffer(torch, workload_512, variant):
     # The benchmark's timed call: one execute_dump with reset into a device buffer the caller
     # owns, which the fused kernel writes directly (no accumulator copy).  Twice in a row into
@@ -736,10 +736,12 @@ def test_workload_512_execute_dump_into_the_callers_buffer(torch, workload_512, 
                  seed=5 + variant)
 
 
-def test_workload_512_host_to_host(torch, workload_512):
+@pytest.mark.parametrize("variant", [1, 10])
+def test_workload_512_host_to_host(torch, workload_512, variant):
     # the benchmark's end-to-end call: pinned host input and output, channel groups pipelined
+    # (each group's launch reads a channel slice of rows that hold all channels)
     with xcorr.Plan(256, 512, 2048) as plan:
-        plan.set_tuning(1, 0, 2, 0)
+        plan.set_tuning(variant, 0, 2, 0)
         xh = torch.from_numpy(np.ascontiguousarray(workload_512)).pin_memory()
         out = plan.execute_dump_host(xh)
         plan.sync()
