@@ -442,6 +442,82 @@ __global__ void __launch_bounds__(256) unpack_cf32_digits_x2_kernel(const float4
   }
 }
 
+// Float input read once: a CTA stages one (channel, window, 32 inputs) slice -- the window's
+// samples x 32 inputs x 8 bytes, 96 KB for a 384-sample window -- in shared memory with 16-byte
+// loads (each time row of the slice is 256 contiguous bytes), takes each input's window maximum
+// from it, then writes the digits from it.  The two-read kernels above read every float twice
+// from HBM: with a CTA per (channel, window, 256 input pairs) the slices in flight far exceed
+// L2.  Here two CTAs of 256 threads share an SM, so one loads while the other converts.  Thread
+// (pair q, time group g) handles inputs 2q, 2q + 1 of the slice at samples g, g + 16, ...; a warp
+// covers two time rows of 16 pairs (512 contiguous bytes), conflict-free.  Needs n_inputs % 32
+// == 0 and a 16-byte aligned input; same arithmetic as the other kernels, so the same results.
+constexpr int kTileInputs = 32;
+constexpr int kTilePairs = kTileInputs / 2;
+constexpr int kTileGroups = 16;
+constexpr int kTileThreads = kTilePairs * kTileGroups;
+__global__ void __launch_bounds__(kTileThreads, 2) unpack_cf32_digits_tile_kernel(
+    const float4* __restrict__ in, uint16_t* __restrict__ planes, int16_t* __restrict__ exps, int n_time, int n_chan,
+    int c0, int nc, int n_inputs, int ni_pad, int64_t comp_stride, int window, int exp_windows) {
+  extern __shared__ float4 slice[];  // [window][kTilePairs]
+  __shared__ uint32_t part[2][kTileGroups][kTilePairs];
+  __shared__ int win_e[2][kTilePairs];
+  const int n_w = (n_time + window - 1) / window;
+  const int n_groups = n_inputs / kTileInputs;
+  const int half = n_inputs / 2;
+  const int q = threadIdx.x % kTilePairs, g = threadIdx.x / kTilePairs;
+  for (int64_t blk = blockIdx.x; blk < (int64_t)nc * n_w * n_groups; blk += gridDim.x) {
+    const int ig = static_cast<int>(blk % n_groups);
+    const int64_t rest = blk / n_groups;
+    const int w = static_cast<int>(rest % n_w);
+    const int c = c0 + static_cast<int>(rest / n_w);
+    const int t0 = w * window, len = min(n_time, t0 + window) - t0;
+    // the slice's rows into shared memory, once
+    const float4* col = in + (int64_t)c * half + ig * kTilePairs + q;
+    const int64_t row_step = (int64_t)n_chan * half;
+    for (int r = g; r < len; r += kTileGroups) slice[r * kTilePairs + q] = __ldg(col + (t0 + r) * row_step);
+    __syncthreads();
+    uint32_t mb0 = 0u, mb1 = 0u;
+    for (int r = g; r < len; r += kTileGroups) {
+      const float4 v = slice[r * kTilePairs + q];
+      mb0 = max(mb0, max(abs_bits(v.x), abs_bits(v.y)));
+      mb1 = max(mb1, max(abs_bits(v.z), abs_bits(v.w)));
+    }
+    part[0][g][q] = mb0;
+    part[1][g][q] = mb1;
+    __syncthreads();
+    if (threadIdx.x < 2 * kTilePairs) {
+      const int k = threadIdx.x / kTilePairs, pq = threadIdx.x % kTilePairs;
+      uint32_t m = 0u;
+#pragma unroll
+      for (int gg = 0; gg < kTileGroups; ++gg) m = max(m, part[k][gg][pq]);
+      const int e = window_exponent(m);
+      win_e[k][pq] = e;
+      exps[((int64_t)c * exp_windows + w) * ni_pad + ig * kTileInputs + 2 * pq + k] = static_cast<int16_t>(e);
+    }
+    __syncthreads();
+    float s0a, s0b, s1a, s1b;
+    window_scale(win_e[0][q], s0a, s0b);
+    window_scale(win_e[1][q], s1a, s1b);
+    uint32_t* base = reinterpret_cast<uint32_t*>(planes + (6 * (int64_t)c) * comp_stride + ig * kTileInputs + 2 * q);
+    const int64_t cs = comp_stride / 2;  // in uint32 units (comp_stride is a multiple of 16)
+    for (int r = g; r < len; r += kTileGroups) {
+      const float4 v = slice[r * kTilePairs + q];
+      uint16_t r0[3], m0[3], r1[3], m1[3];
+      digits_of(v.x, s0a, s0b, r0);
+      digits_of(v.y, s0a, s0b, m0);
+      digits_of(v.z, s1a, s1b, r1);
+      digits_of(v.w, s1a, s1b, m1);
+      uint32_t* row = base + (int64_t)(t0 + r) * (ni_pad / 2);
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc) {
+        row[pc * cs] = r0[pc] | (static_cast<uint32_t>(r1[pc]) << 16);
+        row[(3 + pc) * cs] = m0[pc] | (static_cast<uint32_t>(m1[pc]) << 16);
+      }
+    }
+    __syncthreads();  // the slice is refilled by the next block of work
+  }
+}
+
 int64_t grid_for(int64_t work, int num_sms) {
   int64_t blocks = (work + 255) / 256;
   const int64_t cap = (int64_t)num_sms * 16;
@@ -473,6 +549,26 @@ cudaError_t launch_unpack_cf32_digits(const float* in, uint16_t* planes, int16_t
                                       int c0, int nc, int n_inputs, int ni_pad, int max_time, int window,
                                       int exp_windows, cudaStream_t stream) {
   const int64_t comp_stride = (int64_t)max_time * ni_pad;
+  if (n_inputs % kTileInputs == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0) {
+    // read once through shared memory: 2 CTAs per SM, each looping over its slices
+    const size_t smem = (size_t)window * kTilePairs * sizeof(float4);
+    static int attr_device = -1;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && attr_device != dev) {
+      e = cudaFuncSetAttribute(unpack_cf32_digits_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e == cudaSuccess) attr_device = dev;
+    }
+    if (e != cudaSuccess) return e;
+    const int64_t slices = (int64_t)nc * ((n_time + window - 1) / window) * (n_inputs / kTileInputs);
+    const int64_t grid = slices < 2LL * sms ? slices : 2LL * sms;
+    unpack_cf32_digits_tile_kernel<<<(unsigned)grid, kTileThreads, smem, stream>>>(
+        reinterpret_cast<const float4*>(in), planes, exps, n_time, n_chan, c0, nc, n_inputs, ni_pad, comp_stride,
+        window, exp_windows);
+    return cudaGetLastError();
+  }
   const bool x2 = n_inputs % 2 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0;
   const int64_t work = (int64_t)nc * ((n_time + window - 1) / window) * (x2 ? n_inputs / 2 : n_inputs);
   int64_t blocks = (work + 255) / 256;

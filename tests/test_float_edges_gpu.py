@@ -9,9 +9,12 @@ its channel.  The tolerance is the float path's own: per entry
 plus 2^-120 for entries whose exact value lies below the normal float range,
 where a float result can only be a subnormal or zero.
 
-Every case runs with the input at three placements: 16-byte aligned (the
-two-inputs-per-thread unpack) and at byte offsets 4 and 8 (the scalar unpack,
-which reads single floats).
+Every case runs with the input at four placements: 16-byte aligned with an
+input count that is a multiple of 32 (the unpack that stages each window in
+shared memory and reads it once; the stations are padded with zero stations,
+and the original triangle is the first N_i (N_i + 1) / 2 entries of the
+padded one), 16-byte aligned otherwise (the two-inputs-per-thread unpack), and
+at byte offsets 4 and 8 (the scalar unpack, which reads single floats).
 """
 
 import numpy as np
@@ -22,7 +25,7 @@ from paper_1401_8288_gb300 import synth, xcorr
 
 pytestmark = pytest.mark.gpu
 
-LAYOUTS = ["aligned", "offset4", "offset8"]
+LAYOUTS = ["tile", "aligned", "offset4", "offset8"]
 REL = 1e-6
 FLOOR = 2.0**-120
 
@@ -39,14 +42,20 @@ def torch():
 def correlate(torch, x, layout, chunks=None):
     """One integration of x (host float32 [t][c][s][2][2]) on the tensor engine,
     the input placed as layout says; chunks: several executes."""
+    n_pairs = (2 * x.shape[2]) * (2 * x.shape[2] + 1) // 2
+    if layout == "tile":
+        pad = (-x.shape[2]) % 16
+        x = np.concatenate([x, np.zeros(x.shape[:2] + (pad,) + x.shape[3:], dtype=x.dtype)], axis=2)
+    elif layout == "aligned":
+        assert (2 * x.shape[2]) % 32 != 0, "this placement is for input counts the staged unpack does not take"
     n_time, n_chan, n_sta = x.shape[0], x.shape[1], x.shape[2]
     chunks = chunks or [n_time]
     flat = torch.from_numpy(np.ascontiguousarray(x).reshape(-1)).cuda()
-    off = {"aligned": 0, "offset4": 4, "offset8": 8}[layout]
+    off = {"tile": 0, "aligned": 0, "offset4": 4, "offset8": 8}[layout]
     buf = torch.zeros(flat.numel() + 8, dtype=torch.float32, device="cuda")
     buf[off // 4:off // 4 + flat.numel()] = flat
     base = buf.data_ptr() + off
-    assert (base % 16 == 0) == (layout == "aligned")
+    assert (base % 16 == 0) == (layout in ("tile", "aligned"))
     row = n_chan * n_sta * 2 * 2 * 4  # bytes of one time sample
     with xcorr.Plan(n_sta, n_chan, max(chunks), fmt="cf32", engine="tensor") as plan:
         t0 = 0
@@ -55,7 +64,7 @@ def correlate(torch, x, layout, chunks=None):
             t0 += k
         out = plan.dump(stream=0)
         plan.sync(0)
-        return out.cpu().numpy().astype(np.float64)
+        return out.cpu().numpy().astype(np.float64)[:, :n_pairs]
 
 
 def pair_axes(n_inputs):
