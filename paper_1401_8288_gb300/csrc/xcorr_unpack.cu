@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(256) unpack_cf32_digits_x2_kernel(const float4
 
 // Float input read once: a CTA stages one (channel, window, 32 inputs) slice -- the window's
 // samples x 32 inputs x 8 bytes, 96 KB for a 384-sample window -- in shared memory with 16-byte
-// loads (each time row of the slice is 256 contiguous bytes), takes each input's window maximum
+// asynchronous copies (each time row of the slice is 256 contiguous bytes), takes each input's window maximum
 // from it, then writes the digits from it.  The two-read kernels above read every float twice
 // from HBM: with a CTA per (channel, window, 256 input pairs) the slices in flight far exceed
 // L2.  Here two CTAs of 256 threads share an SM, so one loads while the other converts.  Thread
@@ -471,10 +471,16 @@ __global__ void __launch_bounds__(kTileThreads, 2) unpack_cf32_digits_tile_kerne
     const int w = static_cast<int>(rest % n_w);
     const int c = c0 + static_cast<int>(rest / n_w);
     const int t0 = w * window, len = min(n_time, t0 + window) - t0;
-    // the slice's rows into shared memory, once
+    // the slice's rows into shared memory, once: asynchronous 16-byte copies, all of a thread's
+    // rows in flight together
     const float4* col = in + (int64_t)c * half + ig * kTilePairs + q;
     const int64_t row_step = (int64_t)n_chan * half;
-    for (int r = g; r < len; r += kTileGroups) slice[r * kTilePairs + q] = __ldg(col + (t0 + r) * row_step);
+    for (int r = g; r < len; r += kTileGroups) {
+      const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&slice[r * kTilePairs + q]));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(col + (t0 + r) * row_step)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     uint32_t mb0 = 0u, mb1 = 0u;
     for (int r = g; r < len; r += kTileGroups) {
