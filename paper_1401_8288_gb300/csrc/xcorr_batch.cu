@@ -157,6 +157,9 @@ xcorr_status build_tables(xcorr_batch b, const void* const* d_ins, void* const* 
   for (int s = 0; s < b->n; ++s) {
     const int cls_s = fused ? ta_class(b->sub_shape[s]) : 0;
     if (fused && cls_s < 0) {  // runs alone: its launcher reads the buffers it is given
+      if (d_ins && reinterpret_cast<uintptr_t>(d_ins[s]) % 16)
+        return bfail(XCORR_ERR_INVALID_ARG, "subarray " + std::to_string(s) + ": the fused kernels need a 16-byte "
+                                                                            "aligned input");
       b->fdescs_host[s].out = d_outs ? static_cast<int2*>(d_outs[s]) : nullptr;
       b->ins[s] = d_ins ? d_ins[s] : nullptr;
       continue;

@@ -31,3 +31,37 @@ def test_reference_arm_line():
 def test_reference_arm_declines_the_packet_workload():
     d = run_bench("--impl", "reference", "--workload", "stream1024", "--steps", "1", "--warmup", "0")
     assert d["impl"] == "reference" and "unavailable" in d
+
+
+def load_bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_the_timed_output_check_passes_the_oracle_and_flags_one_changed_entry():
+    # bench.py compares the last timed step's output with the oracle; here the "output" is
+    # the oracle's own result (must pass) and the same with one entry changed (must fail)
+    import numpy as np
+
+    import oracle
+    from paper_1401_8288_gb300 import synth
+    bench = load_bench()
+    x = synth.uniform_ci4(64, 6, 20, seed=3)
+    good = oracle.correlate(oracle.FMT_CI4, x).astype(np.int32)
+    assert bench.oracle_check(good, x, "ci4", [0, 5], 50, seed=1)["exact"]
+    for c, pair, comp in ((0, 7, 1), (3, 500, 0)):  # a checked channel; a channel only sampled
+        bad = good.copy()
+        bad[c, pair, comp] += 1
+        r = bench.oracle_check(bad, x, "ci4", [0, 5], 2000, seed=1)
+        assert not r["exact"], (c, pair, comp)
+    # float input: within 1e-6 of sqrt(V_ii V_jj) passes, a 1e-5 relative error on one entry fails
+    y = synth.gaussian_cf32(64, 3, 10, seed=4)
+    fgood = oracle.correlate(oracle.FMT_CF32, y).astype(np.float32)
+    r = bench.oracle_check(fgood, y, "cf32", [0, 2], 200, seed=2)
+    assert r["exact"] and r["max_normalised_error"] < 1e-6
+    fbad = fgood.copy()
+    fbad[2, 11, 0] += 1e-5 * abs(float(fbad[2, 11, 0])) + 1e-3
+    assert not bench.oracle_check(fbad, y, "cf32", [0, 2], 200, seed=2)["exact"]
