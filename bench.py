@@ -59,8 +59,9 @@ WORKLOADS = {
                         mix=dict(count=64, inputs=(16, 128), channels=(16, 256), samples=(512, 4096))),
     # the streaming server: F-engine packets -> device ring -> X-stage -> dumps (see stream_arm)
     # the engine choice for small problems: both engines over a grid of small sizes (see sweep_arm)
-    "engine_sweep": dict(name="4-bit, inputs 2..256, channels 16..256, K 256..2048: tensor (default and "
-                              "small-problem shapes) vs CUDA-core", seed=14018288 + 6, fmt="ci4", dtype="e4m3"),
+    "engine_sweep": dict(name="4-bit, inputs 2..256, channels 16..256, K 256..2048: tensor (a plan's first "
+                              "shape and the small-problem shape) vs CUDA-core; 8-bit, inputs 2..256, channels "
+                              "16..64, K 256..1024: tensor vs CUDA-core", seed=14018288 + 6, fmt="ci4", dtype="e4m3"),
     "stream1024": dict(name="1024 inputs (512 stations x 2 pols), 1024 channels, K=8192 per dump, "
                             "4+4-bit Gaussian in 8 KB packets (4 samples x 128 channels x 16 "
                             "inputs) + 16 B header, ring of 4 blocks of 2048 samples",
@@ -499,50 +500,58 @@ def sweep_arm(args) -> int:
     rows = []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = max(args.steps, 20)
-    for n_in in (2, 8, 16, 32, 64, 128, 256):
-        for n_chan in (16, 64, 256):
-            for n_time in (256, 1024, 2048):
-                xd = synth.uniform_ci4_torch(n_time, n_chan, n_in // 2, seed=n_in * 7 + n_chan + n_time)
-                n_pairs = costmodel.n_pairs(n_in)
-                out = torch.empty((n_chan, n_pairs, 2), dtype=torch.int32, device="cuda")
-                row = {"n_inputs": n_in, "n_channels": n_chan, "n_time": n_time}
-                for label, engine, tuning in (("tensor_default", "tensor", None), ("tensor_small", "tensor", 10),
-                                              ("cuda_core", "cuda_core", None)):
-                    with xcorr.Plan(n_in // 2, n_chan, n_time, engine=engine) as plan:
-                        if tuning is not None:
-                            plan.set_tuning(tuning, 0, 2, 0)
-                        for _ in range(max(args.warmup, 3)):
-                            plan.execute_dump(xd, out)
-                        torch.cuda.synchronize()
-                        ev0.record()
-                        for _ in range(reps):
-                            plan.execute_dump(xd, out)
-                        ev1.record()
-                        torch.cuda.synchronize()
-                        row[label + "_eager_us"] = round(1e3 * ev0.elapsed_time(ev1) / reps, 2)
-                        # the same call, 20 times in one CUDA graph: the device's own time per call
-                        graph = torch.cuda.CUDAGraph()
-                        with torch.cuda.graph(graph):
-                            for _ in range(20):
-                                plan.execute_dump(xd, out)
-                        for _ in range(2):
-                            graph.replay()
-                        torch.cuda.synchronize()
-                        n_rep = max(1, reps // 20)
-                        ev0.record()
-                        for _ in range(n_rep):
-                            graph.replay()
-                        ev1.record()
-                        torch.cuda.synchronize()
-                        row[label + "_us"] = round(1e3 * ev0.elapsed_time(ev1) / (20 * n_rep), 2)
-                        plan.sync()
-                        del graph
-                nbytes = xd.numel() + out.numel() * 4
-                best = min(("tensor_default", "tensor_small", "cuda_core"), key=lambda k: row[k + "_us"])
-                row["best"] = best
-                row["best_hbm_gbs"] = round(nbytes / (row[best + "_us"] * 1e-6) / 1e9, 1)
-                row["tcmacs_best"] = round(costmodel.cmacs(n_chan, n_time, n_in) / (row[best + "_us"] * 1e-6) / 1e12, 4)
-                rows.append(row)
+    grid = [("ci4", n_in, n_chan, n_time) for n_in in (2, 8, 16, 32, 64, 128, 256) for n_chan in (16, 64, 256)
+            for n_time in (256, 1024, 2048)]
+    grid += [("ci8", n_in, n_chan, n_time) for n_in in (2, 8, 16, 64, 256) for n_chan in (16, 64)
+             for n_time in (256, 1024)]
+    for fmt, n_in, n_chan, n_time in grid:
+        seed = n_in * 7 + n_chan + n_time
+        if fmt == "ci4":
+            xd = synth.uniform_ci4_torch(n_time, n_chan, n_in // 2, seed=seed)
+        else:
+            xd = torch.from_numpy(synth.uniform_ci8(n_time, n_chan, n_in // 2, seed=seed)).cuda()
+        n_pairs = costmodel.n_pairs(n_in)
+        out = torch.empty((n_chan, n_pairs, 2), dtype=torch.int32, device="cuda")
+        row = {"fmt": fmt, "n_inputs": n_in, "n_channels": n_chan, "n_time": n_time}
+        shapes = (("tensor_default", "tensor", None), ("tensor_small", "tensor", 10),
+                  ("cuda_core", "cuda_core", None)) if fmt == "ci4" else \
+                 (("tensor_default", "tensor", None), ("cuda_core", "cuda_core", None))
+        for label, engine, tuning in shapes:
+            with xcorr.Plan(n_in // 2, n_chan, n_time, fmt=fmt, engine=engine) as plan:
+                if tuning is not None:
+                    plan.set_tuning(tuning, 0, 2, 0)
+                for _ in range(max(args.warmup, 3)):
+                    plan.execute_dump(xd, out)
+                torch.cuda.synchronize()
+                ev0.record()
+                for _ in range(reps):
+                    plan.execute_dump(xd, out)
+                ev1.record()
+                torch.cuda.synchronize()
+                row[label + "_eager_us"] = round(1e3 * ev0.elapsed_time(ev1) / reps, 2)
+                # the same call, 20 times in one CUDA graph: the device's own time per call
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    for _ in range(20):
+                        plan.execute_dump(xd, out)
+                for _ in range(2):
+                    graph.replay()
+                torch.cuda.synchronize()
+                n_rep = max(1, reps // 20)
+                ev0.record()
+                for _ in range(n_rep):
+                    graph.replay()
+                ev1.record()
+                torch.cuda.synchronize()
+                row[label + "_us"] = round(1e3 * ev0.elapsed_time(ev1) / (20 * n_rep), 2)
+                plan.sync()
+                del graph
+        nbytes = xd.numel() * xd.element_size() + out.numel() * 4
+        best = min((lab for lab, _, _ in shapes), key=lambda k: row[k + "_us"])
+        row["best"] = best
+        row["best_hbm_gbs"] = round(nbytes / (row[best + "_us"] * 1e-6) / 1e9, 1)
+        row["tcmacs_best"] = round(costmodel.cmacs(n_chan, n_time, n_in) / (row[best + "_us"] * 1e-6) / 1e12, 4)
+        rows.append(row)
     if info.rank == 0:
         emit({"metric": "per-call time of one execute_dump by engine over small sizes", "unit": "us",
               "n_gpus": info.world, "steps": reps, "warmup": args.warmup, "higher_is_better": False,
