@@ -88,9 +88,9 @@ typedef enum {
 typedef enum { XCORR_IN_CI4 = 0, XCORR_IN_CI8 = 1, XCORR_IN_CF32 = 2 } xcorr_in_fmt;
 
 typedef enum {
-    XCORR_ENGINE_AUTO = 0,      /* the faster engine as measured on GB300: CUDA-core for
-                                   integer input with fewer than 16 inputs and at most 16
-                                   channels, the tensor cores otherwise                   */
+    XCORR_ENGINE_AUTO = 0,      /* the faster engine as measured on GB300: CUDA-core at
+                                   most 16 channels with fewer than 16 inputs (CI4) or at
+                                   most 64 inputs (CI8), the tensor cores otherwise       */
     XCORR_ENGINE_TENSOR = 1,    /* tcgen05 tensor-core X kernel                          */
     XCORR_ENGINE_CUDA_CORE = 2  /* plain CUDA-core (dp4a) X kernel, integer formats only */
 } xcorr_engine;
@@ -151,9 +151,9 @@ typedef struct {
  * kernels.  *out receives the plan, or NULL on failure.
  * Engines: TENSOR uses the tcgen05 kernels for every format (4-bit as E4M3,
  * int8 as BF16, float as three BF16 pieces); CUDA_CORE takes CI4 / CI8; AUTO
- * takes CUDA_CORE for integer input with fewer than 16 inputs and at most 16
- * channels (where its single launch was measured faster than the tensor
- * path's unpack + X) and TENSOR otherwise.  A 4-bit tensor plan starts on
+ * takes CUDA_CORE for at most 16 channels with fewer than 16 inputs (CI4) or at
+ * most 64 inputs (CI8), where its single launch was measured faster than the
+ * tensor path's unpack + X, and TENSOR otherwise.  A 4-bit tensor plan starts on
  * launch shape 10 (the small-problem layout) when N_i <= 64 and either
  * max_time_per_exec >= 1024 or n_channels >= 256, else on shape 4.
  * max_integration (xcorr_plan_query) is 16,777,215 samples for CI4, 65,535

@@ -282,13 +282,15 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
   if (c.engine != XCORR_ENGINE_AUTO && c.engine != XCORR_ENGINE_TENSOR && c.engine != XCORR_ENGINE_CUDA_CORE)
     return fail(XCORR_ERR_INVALID_ARG, "unknown engine");
 
-  // AUTO: the engine the per-call device times favour (graph-replayed execute_dump, 4-bit input,
-  // inputs 2-256, channels 16-256, K 256-2048): the CUDA-core kernel only where the problem is
-  // smaller than one tensor tile on both sides, fewer than 16 inputs (the tensor path then unpacks
-  // to planes first: two launches) and at most 16 channels; the tensor cores everywhere else.
+  // AUTO: the engine the per-call device times favour (graph-replayed execute_dump; 4-bit input
+  // over inputs 2-256, channels 16-256, K 256-2048; int8 over inputs 2-256, channels 16-64,
+  // K 256-1024).  The CUDA-core kernel wins only at most 16 channels: for 4-bit input below 16
+  // inputs (the tensor path then unpacks to planes first: two launches), for int8 input up to 64
+  // inputs (its tensor path always unpacks to BF16 planes first); the tensor cores everywhere else.
+  const int cc_inputs = c.fmt == XCORR_IN_CI4 ? 15 : c.fmt == XCORR_IN_CI8 ? 64 : 0;
   const int engine = c.engine != XCORR_ENGINE_AUTO ? c.engine
-                     : (c.fmt != XCORR_IN_CF32 && 2 * c.n_stations < 16 && c.n_channels <= 16) ? XCORR_ENGINE_CUDA_CORE
-                                                                                            : XCORR_ENGINE_TENSOR;
+                     : (c.n_stations <= cc_inputs / 2 && c.n_channels <= 16) ? XCORR_ENGINE_CUDA_CORE
+                                                                            : XCORR_ENGINE_TENSOR;
   if (engine == XCORR_ENGINE_CUDA_CORE && c.fmt == XCORR_IN_CF32)
     return fail(XCORR_ERR_UNSUPPORTED, "the CUDA-core engine takes integer input only");
 

@@ -249,10 +249,11 @@ def test_budget_and_query(torch):
 
 
 def test_auto_engine_and_default_shape_follow_the_measured_rule(torch):
-    # AUTO: CUDA-core only for integer input below 16 inputs and at most 16 channels
+    # AUTO: CUDA-core only at most 16 channels, below 16 inputs for 4-bit, up to 64 inputs for int8
     cases = [((4, 8, 1024, "ci4"), xcorr.XCORR_ENGINE_CUDA_CORE), ((4, 16, 256, "ci8"), xcorr.XCORR_ENGINE_CUDA_CORE),
              ((8, 8, 1024, "ci4"), xcorr.XCORR_ENGINE_TENSOR), ((4, 17, 64, "ci4"), xcorr.XCORR_ENGINE_TENSOR),
-             ((2, 4, 64, "cf32"), xcorr.XCORR_ENGINE_TENSOR)]
+             ((32, 16, 1024, "ci8"), xcorr.XCORR_ENGINE_CUDA_CORE), ((33, 16, 1024, "ci8"), xcorr.XCORR_ENGINE_TENSOR),
+             ((32, 17, 1024, "ci8"), xcorr.XCORR_ENGINE_TENSOR), ((2, 4, 64, "cf32"), xcorr.XCORR_ENGINE_TENSOR)]
     for (ns, nc, nt, fmt), engine in cases:
         with xcorr.Plan(ns, nc, nt, fmt=fmt, engine="auto") as plan:
             assert plan.query()["engine"] == engine, (ns, nc, nt, fmt)
@@ -265,6 +266,9 @@ def test_auto_engine_and_default_shape_follow_the_measured_rule(torch):
     x = synth.uniform_ci4(1024, 8, 4, seed=81, lo=-8, hi=7)
     got, _ = run(torch, x, "auto")
     assert np.array_equal(got, oracle.correlate(oracle.FMT_CI4, x))
+    y = synth.uniform_ci8(1024, 16, 32, seed=82)
+    got, _ = run(torch, y, "auto", fmt="ci8")
+    assert np.array_equal(got, oracle.correlate(oracle.FMT_CI8, y))
 
 
 # -------------------------------------------------- int8 on tensor cores ---
