@@ -63,8 +63,6 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kStashCol = 256;                       // 128 columns of corrected Im after the accumulator
 constexpr uint32_t kAcol0 = 384;                          // then the A stages
 constexpr int kStagingBytes = kBlk * kBlk * 4;            // Re accumulator bits of a whole tile pair
-constexpr int kTPitch = 20;                               // Im transpose rows: 16 words + 16 bytes of pad
-constexpr int kTransposeBytes = kEpiWarps * 32 * kTPitch * 4;  // per-warp Im transpose for the stores
 constexpr int kRowcBytes = kBlk * 8;                      // per-row correction constants
 constexpr int kSumsBytes = 2 * 2 * kBlk * 8;              // [item parity][rows I, columns J][input] (8P, 8Q)
 // Every partial sum of u_a u_b is n 2^-18 with 0 <= n <= 450 T (and |n| <= 225 T for Im).
@@ -84,7 +82,7 @@ struct TGeom {
   static constexpr int kAcols = KT / 2;        // one A stage: KT / 4 columns of real codes, then imaginary
   static constexpr int kRowsB = KT / (kDecThreads / 8);  // B rows per decoder thread and stage
   static constexpr int kSteps = KT / 32;                 // MMA steps (32 samples) per stage
-  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kBStage + kStagingBytes + kTransposeBytes + kRowcBytes +
+  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kBStage + kStagingBytes + kRowcBytes +
                                kSumsBytes + kScratchBytes + kBarrierBytes;
   static_assert(KT % 32 == 0, "stages hold whole MMA steps and whole 32-row B passes");
   static_assert(DEC * kAcols <= static_cast<int>(kTmemCols - kAcol0), "A stages fit beside the accumulator");
@@ -200,8 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* raw = smem;
   uint8_t* bpl = raw + RAW * G::kRawStage;
   uint32_t* staging = reinterpret_cast<uint32_t*>(bpl + DEC * G::kBStage);  // Re [row][16-byte chunk ^ swz(row)]
-  uint32_t* transpose = staging + kBlk * kBlk;                               // [warp][32][kTPitch]
-  int2* rowc = reinterpret_cast<int2*>(transpose + kEpiWarps * 32 * kTPitch);  // [row]
+  int2* rowc = reinterpret_cast<int2*>(staging + kBlk * kBlk);                // [row]
   int2* sums = rowc + kBlk;
   int2* scratch = sums + 2 * 2 * kBlk;
   uint64_t* raw_full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(scratch) + kScratchBytes);
@@ -489,11 +486,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Epilogue, warp w = tile rows 32w .. 32w + 31 (TMEM lanes of quarter w).  Phase 1 only moves
     // the accumulator out, so that it is free as soon as possible: Re bits to the shared-memory
     // staging tile, Im bits to the TMEM stash.  Phase 2, while the MMAs run the next tile pair,
-    // converts, applies the offset corrections and writes the rows; Im goes through the warp's
-    // transpose buffer so that four threads write 16 consecutive pairs of one row.
+    // converts, applies the offset corrections and writes the rows.  It reads the stash with
+    // 16-lane x 256-bit loads, which give thread t columns 2 (t % 4), + 1 (and 8 on) of rows
+    // t / 4 and t / 4 + 8, and phase 1 stages each row's Re in that column order, so four threads
+    // write 16 consecutive pairs of a row straight from registers.
     const int r_own = warp * 32 + lane;  // this thread's tile row in phase 1
     const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    uint32_t* tim = transpose + warp * 32 * kTPitch;
     int g = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++g) {
       const TItem it = resolve<BATCH, SMALL, PACK, KT>(p, &raw_map, item, n_items);
@@ -535,9 +533,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld16(taddr + 128 + kChunk * ch, nim);
           tmem_ld_wait();
           tmem_st16(taddr + kStashCol + kChunk * ch, nim);
+          // 16-byte piece q of the chunk holds columns 2q, 2q + 1, 8 + 2q, 9 + 2q (phase 2's order)
 #pragma unroll
-          for (int k = 0; k < kChunk / 4; ++k)
-            srow[((kChunk * ch) / 4 + k) ^ sw] = make_uint4(re[4 * k], re[4 * k + 1], re[4 * k + 2], re[4 * k + 3]);
+          for (int q = 0; q < kChunk / 4; ++q)
+            srow[((kChunk * ch) / 4 + q) ^ sw] = make_uint4(re[2 * q], re[2 * q + 1], re[8 + 2 * q], re[9 + 2 * q]);
         }
         // Re = n_re - 8 P_a - 8 P_b + 128 T,  Im = -n_im - 8 Q_a + 8 Q_b: the row's part
         const int2 rs = sums[(buf * 2) * kBlk + r_own];  // (8P, 8Q) of this row's input
@@ -548,96 +547,109 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty);
+      // phase 2 reads stash lanes that other threads of the warp stored
       tmem_st_wait();
-      // phase 2: four threads per row, four consecutive columns each (16-byte loads of Re, Im and
-      // the column sums; 16-byte stores where the row's pairs are 16-byte aligned)
+      tc_fence_before();
+      __syncwarp();
+      tc_fence_after();
+      // phase 2: thread (rg, q) = (lane / 4, lane % 4) owns rows 32 warp + rg + 8m (m = 0..3) and,
+      // in each 16-column chunk, columns 2q, 2q + 1, 8 + 2q, 9 + 2q
       const int2* cs = sums + (buf * 2 + (I == J ? 0 : 1)) * kBlk;  // (8P, 8Q) of the columns
       const int q4 = lane & 3, rg = lane >> 2;
+      int2* row_out[4];  // the row's pairs (j = first .. last of the tile), or null
+      int firstm[4], lastm[4];
+      int2 rcm[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int rr = warp * 32 + rg + 8 * m;
+        row_out[m] = nullptr;
+        firstm[m] = 0;
+        lastm[m] = I == J ? rr : kBlk - 1;  // last column of the row in the tile
+        rcm[m] = rowc[rr];
+        if (PACK) {
+          const int blk = rr / n_inputs, cr = c * p.pack_g + blk;
+          if (blk < p.pack_g && cr < p.n_chan) {
+            firstm[m] = blk * n_inputs;
+            const int i = rr - firstm[m];
+            row_out[m] = it.out + (int64_t)cr * it.n_pairs + (int64_t)i * (i + 1) / 2;
+          }
+        } else {
+          const int i = I * kBlk + rr;
+          if (i < n_inputs) row_out[m] = out_c + (int64_t)i * (i + 1) / 2 + J * kBlk;
+        }
+      }
       for (int ch = 0; ch < n_ch; ++ch) {
-        uint32_t im[16];
-        tmem_ld16(taddr + kStashCol + kChunk * ch, im);
-        const int jl0 = kChunk * ch + 4 * q4;  // this thread's first column in the tile
-        const int4 s01 = *reinterpret_cast<const int4*>(cs + jl0);  // (8P, 8Q) of columns jl0, jl0 + 1
-        const int4 s23 = *reinterpret_cast<const int4*>(cs + jl0 + 2);
+        uint32_t im[2][8];  // [rows 0-15 | 16-31 of the warp][2j + h .. : column 8j + 2q + e of row rg + 8h]
+        tmem_ld_16x256b_x2(taddr + kStashCol + kChunk * ch, im[0]);
+        tmem_ld_16x256b_x2(taddr + (16u << 16) + kStashCol + kChunk * ch, im[1]);
+        const int jc = kChunk * ch + 2 * q4;  // this thread's first column in the tile
+        const int4 s0 = *reinterpret_cast<const int4*>(cs + jc);  // (8P, 8Q) of columns jc, jc + 1
+        const int4 s1 = *reinterpret_cast<const int4*>(cs + jc + 8);
+        const int sp[4] = {s0.x, s0.z, s1.x, s1.z}, sq[4] = {s0.y, s0.w, s1.y, s1.w};
         tmem_ld_wait();
-        uint4* trow = reinterpret_cast<uint4*>(tim + lane * kTPitch);
 #pragma unroll
-        for (int k = 0; k < kChunk / 4; ++k) trow[k] = make_uint4(im[4 * k], im[4 * k + 1], im[4 * k + 2], im[4 * k + 3]);
-        __syncwarp();
-#pragma unroll
-        for (int rw = 0; rw < 4; ++rw) {
-          const int rl = 8 * rw + rg, rr = warp * 32 + rl;
-          int i, first = 0;  // the row's input, and its first column in the tile
-          int2* row_out;     // the row's pairs (j = first .. last of the tile)
-          if (PACK) {
-            const int blk = rr / n_inputs, cr = c * p.pack_g + blk;
-            if (blk >= p.pack_g || cr >= p.n_chan) continue;
-            first = blk * n_inputs;
-            i = rr - first;
-            row_out = it.out + (int64_t)cr * it.n_pairs + (int64_t)i * (i + 1) / 2;
-          } else {
-            i = I * kBlk + rr;
-            if (i >= n_inputs) continue;
-            row_out = out_c + (int64_t)i * (i + 1) / 2 + J * kBlk;
-          }
-          const int last = I == J ? rr : kBlk - 1;  // last column of the row in the tile
-          // (first is a multiple of 16 and jl0 of 4: a run of four starts inside the row or wholly before it)
-          if (jl0 > last || jl0 < first) continue;
+        for (int m = 0; m < 4; ++m) {
+          if (row_out[m] == nullptr) continue;
+          const int rr = warp * 32 + rg + 8 * m;
+          const int first = firstm[m], last = lastm[m];
+          if (jc > last || jc + 9 < first) continue;
           const uint4 re4 =
-              *reinterpret_cast<const uint4*>(staging + rr * kBlk + (((jl0 >> 2) ^ staging_swizzle(rr)) << 2));
-          const uint4 im4 = *reinterpret_cast<const uint4*>(tim + rl * kTPitch + 4 * q4);
-          const int2 rc = rowc[rr];
-          const uint32_t vr[4] = {re4.x, re4.y, re4.z, re4.w}, vi[4] = {im4.x, im4.y, im4.z, im4.w};
-          const int sp[4] = {s01.x, s01.z, s23.x, s23.z}, sq[4] = {s01.y, s01.w, s23.y, s23.w};
-          int2 v[4];
+              *reinterpret_cast<const uint4*>(staging + rr * kBlk + ((((kChunk * ch) >> 2) + q4) ^ staging_swizzle(rr)) * 4);
+          const uint32_t vr[4] = {re4.x, re4.y, re4.z, re4.w};
+          const uint32_t* vi = im[m >> 1];
+          const int h = m & 1;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            int nr, ni;
-            if (magic) {
-              nr = __float_as_int(fmaf(__uint_as_float(vr[k]), 262144.0f, kMagic));
-              ni = __float_as_int(fmaf(__uint_as_float(vi[k]), 262144.0f, kMagic));
-            } else {
-              nr = __float2int_rn(__uint_as_float(vr[k]) * 262144.0f);
-              ni = __float2int_rn(__uint_as_float(vi[k]) * 262144.0f);
-            }
-            v[k] = make_int2(nr + rc.x - sp[k], -ni + rc.y + sq[k]);
-          }
-          int2* dst = row_out + (jl0 - first);
-          const int nv = last - jl0 + 1 < 4 ? last - jl0 + 1 : 4;
-          if (SMALL && p.atomic_out) {  // time-split items of one tile add into the same pairs
+          for (int jj = 0; jj < 2; ++jj) {  // columns jc + 8 jj, + 1
+            const int j0 = jc + 8 * jj;
+            int2 v[2];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              if (k < nv) {
-                atomicAdd(&dst[k].x, v[k].x);
-                atomicAdd(&dst[k].y, v[k].y);
+            for (int e = 0; e < 2; ++e) {
+              const uint32_t xr = vr[2 * jj + e], xi = vi[4 * jj + 2 * h + e];
+              int nr, ni;
+              if (magic) {
+                nr = __float_as_int(fmaf(__uint_as_float(xr), 262144.0f, kMagic));
+                ni = __float_as_int(fmaf(__uint_as_float(xi), 262144.0f, kMagic));
+              } else {
+                nr = __float2int_rn(__uint_as_float(xr) * 262144.0f);
+                ni = __float2int_rn(__uint_as_float(xi) * 262144.0f);
               }
+              v[e] = make_int2(nr + rcm[m].x - sp[2 * jj + e], -ni + rcm[m].y + sq[2 * jj + e]);
             }
-          } else if (nv == 4 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
-            int4* d4 = reinterpret_cast<int4*>(dst);
-            int4 w0 = make_int4(v[0].x, v[0].y, v[1].x, v[1].y), w1 = make_int4(v[2].x, v[2].y, v[3].x, v[3].y);
-            if (it.accumulate) {
-              const int4 o0 = d4[0], o1 = d4[1];
-              w0 = make_int4(w0.x + o0.x, w0.y + o0.y, w0.z + o0.z, w0.w + o0.w);
-              w1 = make_int4(w1.x + o1.x, w1.y + o1.y, w1.z + o1.z, w1.w + o1.w);
-            }
-            d4[0] = w0;
-            d4[1] = w1;
-          } else {
+            // (first is a multiple of 16 and j0 even: a pair of columns starts inside the row or before it)
+            if (j0 > last || j0 < first) continue;
+            int2* dst = row_out[m] + (j0 - first);
+            const int nv = j0 + 1 <= last ? 2 : 1;
+            if (SMALL && p.atomic_out) {  // time-split items of one tile add into the same pairs
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              if (k < nv) {
-                int2 w = v[k];
-                if (it.accumulate) {
-                  const int2 o = dst[k];
-                  w.x += o.x;
-                  w.y += o.y;
+              for (int e = 0; e < 2; ++e) {
+                if (e < nv) {
+                  atomicAdd(&dst[e].x, v[e].x);
+                  atomicAdd(&dst[e].y, v[e].y);
                 }
-                dst[k] = w;
+              }
+            } else if (nv == 2 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+              int4 w = make_int4(v[0].x, v[0].y, v[1].x, v[1].y);
+              if (it.accumulate) {
+                const int4 o = *reinterpret_cast<const int4*>(dst);
+                w = make_int4(w.x + o.x, w.y + o.y, w.z + o.z, w.w + o.w);
+              }
+              *reinterpret_cast<int4*>(dst) = w;
+            } else {
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                if (e < nv) {
+                  int2 w = v[e];
+                  if (it.accumulate) {
+                    const int2 o = dst[e];
+                    w.x += o.x;
+                    w.y += o.y;
+                  }
+                  dst[e] = w;
+                }
               }
             }
           }
         }
-        __syncwarp();
       }
       // the input sums are free
       __syncwarp();
