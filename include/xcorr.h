@@ -122,7 +122,7 @@ typedef struct {
                            128 x (2 + 2), 96 x (3 + 2), 64 x (4 + 4) samples (4 is the
                            default of a 4-bit plan); 7 .. 9: pairs of SMs (a thread-block
                            cluster of 2, one cta_group::2 MMA) sharing a column tile,
-                           rings of 96 x (2 + 3), 128 x (2 + 2), 96 x (2 + 4) samples;
+                           rings of 96 x (2 + 3), 128 x (2 + 2), 128 x (2 + 3) samples;
                            10: the tensor-memory-A kernel's small-problem layout,
                            128 x (2 + 2): for N_i <= 64, 128 / N_i channels side by
                            side in one 128-row tile; and when a launch has fewer tiles

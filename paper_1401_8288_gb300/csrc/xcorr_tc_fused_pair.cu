@@ -69,9 +69,6 @@ constexpr int kHalf = 64;                                 // column-tile inputs 
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kStashCol = 256;                       // Im of the first STASH column chunks after the accumulator
 constexpr int kStagingBytes = kBlk * kBlk * 4;            // Re accumulator bits of a whole tile pair
-constexpr int kTPitch = 20;                               // Im transpose rows: 16 words + 16 bytes of pad
-constexpr int kTransposeBytes = kEpiWarps * 32 * kTPitch * 4;
-constexpr int kRowcBytes = kBlk * 8;                      // per-row correction constants
 constexpr int kSumsBytes = 2 * 2 * kBlk * 8;              // [item parity][rows R, columns S][input] (8P, 8Q)
 // Every partial sum of u_a u_b is n 2^-18 with 0 <= n <= 450 T (and |n| <= 225 T for Im).
 // For T <= kMagicSamples, |n| < 2^22 and n + 1.5 2^23 is exact in FP32, so one FFMA
@@ -102,8 +99,8 @@ struct PGeom {
   static constexpr int kAcols = KT / 2;      // one A stage: KT / 4 columns of real codes, then imaginary
   static constexpr int kRowsB = KT / (kGroupWarps * 32 / 4);  // B rows per decoder thread and stage
   static constexpr int kSteps = KT / 32;                 // MMA steps (32 samples) per stage
-  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kBStage + kStagingBytes + kImHiBytes + kTransposeBytes +
-                               kRowcBytes + kSumsBytes + kScratchBytes + kRscratchBytes + kBarrierBytes;
+  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kBStage + kStagingBytes + kImHiBytes + kSumsBytes +
+                               kScratchBytes + kRscratchBytes + kBarrierBytes;
   static_assert(KT % 32 == 0, "stages hold whole MMA steps and whole 32-row B passes");
   // each decoder group waits only on its own raw slots (stage s uses slot s % RAW, decoded by group
   // s % 2), so no group can test a raw barrier a phase ahead of another group's fill
@@ -172,9 +169,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   uint8_t* bpl = raw + RAW * G::kRawStage;  // [stage][real plane | imaginary plane]
   uint32_t* staging = reinterpret_cast<uint32_t*>(bpl + DEC * G::kBStage);  // Re [row][16-byte chunk ^ swz(row)]
   uint32_t* im_hi = staging + kBlk * kBlk;                 // Im past the stash, [row][16-byte chunk ^ swz(row)]
-  uint32_t* transpose = im_hi + G::kImHiBytes / 4;         // [warp][32][kTPitch]
-  int2* rowc = reinterpret_cast<int2*>(transpose + kEpiWarps * 32 * kTPitch);  // [row]
-  int2* sums = rowc + kBlk;
+  int2* sums = reinterpret_cast<int2*>(im_hi + G::kImHiBytes / 4);
   int2* scratch = sums + 2 * 2 * kBlk;
   int2* rscratch = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(scratch) + kScratchBytes);
   uint64_t* raw_full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(rscratch) + kRscratchBytes);
@@ -534,9 +529,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     // it is free as soon as possible; phase 2, while the MMAs run the next item, converts, applies
     // the offset corrections and writes.  A transposed item writes V[b][a], b in the column tile:
     // lane a of warp w holds a's row of W, so the warp's 32 values of output row b are consecutive.
+    // Otherwise phase 2 reads the Im stash with 16-lane x 256-bit loads, which give thread t
+    // columns 2 (t % 4), + 1 (and 8 on) of rows t / 4 and t / 4 + 8; phase 1 stages each row's Re
+    // and the rest of its Im in that column order, so four threads write 16 consecutive pairs of a
+    // row straight from registers.
     const int r_own = warp * 32 + lane;  // this thread's tile row in phase 1
     const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    uint32_t* tim = transpose + warp * 32 * kTPitch;
     const uint32_t tempty_even = smem_cluster(tempty, 0);
     const uint32_t sink_even = smem_cluster(sink + kSignalBytes * (kDecWarps + warp), 0);
     const uint32_t sempty_peer = smem_cluster(sempty, peer);
@@ -596,22 +594,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           tmem_ld16(taddr + re_col, re);
           tmem_ld16(taddr + re_col + kHalf, nim);
           tmem_ld_wait();
+          // 16-byte piece q of a chunk holds columns 2q, 2q + 1, 8 + 2q, 9 + 2q (phase 2's order)
           if (ch < STASH) {
             tmem_st16(taddr + kStashCol + kChunk * ch, nim);
           } else {
 #pragma unroll
-            for (int k = 0; k < kChunk / 4; ++k)
-              hrow[((kChunk * (ch - STASH)) / 4 + k) ^ sw] =
-                  make_uint4(nim[4 * k], nim[4 * k + 1], nim[4 * k + 2], nim[4 * k + 3]);
+            for (int q = 0; q < kChunk / 4; ++q)
+              hrow[((kChunk * (ch - STASH)) / 4 + q) ^ sw] =
+                  make_uint4(nim[2 * q], nim[2 * q + 1], nim[8 + 2 * q], nim[9 + 2 * q]);
           }
 #pragma unroll
-          for (int k = 0; k < kChunk / 4; ++k)
-            srow[((kChunk * ch) / 4 + k) ^ sw] = make_uint4(re[4 * k], re[4 * k + 1], re[4 * k + 2], re[4 * k + 3]);
+          for (int q = 0; q < kChunk / 4; ++q)
+            srow[((kChunk * ch) / 4 + q) ^ sw] = make_uint4(re[2 * q], re[2 * q + 1], re[8 + 2 * q], re[9 + 2 * q]);
         }
-        // W = n_re - 8 P_a - 8 P_b + 128 T  +  i (-n_im - 8 Q_a + 8 Q_b): the row's part
-        const int2 rs = sums[(buf * 2) * kBlk + r_own];  // (8P, 8Q) of this row's input
-        rowc[r_own] = make_int2(t128 - rs.x - (magic ? kMagicBits : 0), -rs.y + (magic ? kMagicBits : 0));
       }
+      // W = n_re - 8 P_a - 8 P_b + 128 T  +  i (-n_im - 8 Q_a + 8 Q_b): the row's part
+      const int2 rs = sums[(buf * 2) * kBlk + r_own];  // (8P, 8Q) of this row's input
+      const int2 rc_own = make_int2(t128 - rs.x - (magic ? kMagicBits : 0), -rs.y + (magic ? kMagicBits : 0));
       // the accumulator (columns 0-255) is free once its loads have landed; the stash stores
       // (columns 256 .. 256 + 16 STASH - 1) need only land before phase 2 reads them
       tc_fence_before();
@@ -624,11 +623,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         else
           mbar_arrive(tempty);
       }
+      // phase 2 reads stash lanes that other threads of the warp stored
       tmem_st_wait();
+      tc_fence_before();
+      __syncwarp();
+      tc_fence_after();
       const int2* cs = sums + (buf * 2 + 1) * kBlk;  // (8P, 8Q) of the columns, both halves
       if (it.transposed) {
         // V[S*128 + b][R*128 + a] = conj(W[a][b]) = (W.re, -W.im)
-        const int2 rc = rowc[r_own];
+        const int2 rc = rc_own;
         const int a_col = R * kBlk + r_own;
         const int sw = staging_swizzle(r_own);
         for (int ch = 0; ch < n_ch; ++ch) {
@@ -636,18 +639,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           if (ch < STASH) tmem_ld16(taddr + kStashCol + kChunk * ch, im);
           uint32_t re[16];
 #pragma unroll
-          for (int k = 0; k < kChunk / 4; ++k) {
-            const uint4 v = *reinterpret_cast<const uint4*>(staging + r_own * kBlk + ((((kChunk * ch) / 4 + k) ^ sw) << 2));
-            re[4 * k] = v.x, re[4 * k + 1] = v.y, re[4 * k + 2] = v.z, re[4 * k + 3] = v.w;
+          for (int q = 0; q < kChunk / 4; ++q) {
+            const uint4 v = *reinterpret_cast<const uint4*>(staging + r_own * kBlk + ((((kChunk * ch) / 4 + q) ^ sw) << 2));
+            re[2 * q] = v.x, re[2 * q + 1] = v.y, re[8 + 2 * q] = v.z, re[9 + 2 * q] = v.w;
           }
           if (ch < STASH) {
             tmem_ld_wait();
           } else {
 #pragma unroll
-            for (int k = 0; k < kChunk / 4; ++k) {
+            for (int q = 0; q < kChunk / 4; ++q) {
               const uint4 v = *reinterpret_cast<const uint4*>(im_hi + r_own * G::kImHiCols +
-                                                              ((((kChunk * (ch - STASH)) / 4 + k) ^ sw) << 2));
-              im[4 * k] = v.x, im[4 * k + 1] = v.y, im[4 * k + 2] = v.z, im[4 * k + 3] = v.w;
+                                                              ((((kChunk * (ch - STASH)) / 4 + q) ^ sw) << 2));
+              im[2 * q] = v.x, im[2 * q + 1] = v.y, im[8 + 2 * q] = v.z, im[9 + 2 * q] = v.w;
             }
           }
 #pragma unroll
@@ -673,79 +676,85 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           }
         }
       } else {
-        // four threads per row, four consecutive columns each (16-byte loads of Re, Im and the
-        // column sums; 16-byte stores where the row's pairs are 16-byte aligned)
+        // thread (rg, q) = (lane / 4, lane % 4) owns rows 32 warp + rg + 8m (m = 0..3) and, in each
+        // 16-column chunk, columns 2q, 2q + 1, 8 + 2q, 9 + 2q
         const int q4 = lane & 3, rg = lane >> 2;
         for (int ch = 0; ch < n_ch; ++ch) {
           const bool stashed = ch < STASH;  // Im of this chunk in tensor memory (else shared memory)
-          const int jl0 = kChunk * ch + 4 * q4;  // this thread's first column in the tile
-          const int4 s01 = *reinterpret_cast<const int4*>(cs + jl0);  // (8P, 8Q) of columns jl0, jl0 + 1
-          const int4 s23 = *reinterpret_cast<const int4*>(cs + jl0 + 2);
-          if (stashed) {
-            uint32_t im[16];
-            tmem_ld16(taddr + kStashCol + kChunk * ch, im);
-            tmem_ld_wait();
-            uint4* trow = reinterpret_cast<uint4*>(tim + lane * kTPitch);
-#pragma unroll
-            for (int k = 0; k < kChunk / 4; ++k)
-              trow[k] = make_uint4(im[4 * k], im[4 * k + 1], im[4 * k + 2], im[4 * k + 3]);
-            __syncwarp();
-          }
-#pragma unroll
-          for (int rw = 0; rw < 4; ++rw) {
-            const int rl = 8 * rw + rg, rr = warp * 32 + rl, i = R * kBlk + rr;
-            const int last = R == S ? rr : kBlk - 1;  // last column of the row in the tile
-            if (i >= n_inputs || jl0 > last) continue;
-            const uint4 re4 =
-                *reinterpret_cast<const uint4*>(staging + rr * kBlk + (((jl0 >> 2) ^ staging_swizzle(rr)) << 2));
-            const uint4 im4 =
-                stashed ? *reinterpret_cast<const uint4*>(tim + rl * kTPitch + 4 * q4)
-                        : *reinterpret_cast<const uint4*>(im_hi + rr * G::kImHiCols +
-                                                          ((((jl0 - 16 * STASH) >> 2) ^ staging_swizzle(rr)) << 2));
-            const int2 rc = rowc[rr];
-            const uint32_t vr[4] = {re4.x, re4.y, re4.z, re4.w}, vi[4] = {im4.x, im4.y, im4.z, im4.w};
-            const int sp[4] = {s01.x, s01.z, s23.x, s23.z}, sq[4] = {s01.y, s01.w, s23.y, s23.w};
-            int2 v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              int nr, ni;
-              if (magic) {
-                nr = __float_as_int(fmaf(__uint_as_float(vr[k]), 262144.0f, kMagic));
-                ni = __float_as_int(fmaf(__uint_as_float(vi[k]), 262144.0f, kMagic));
-              } else {
-                nr = __float2int_rn(__uint_as_float(vr[k]) * 262144.0f);
-                ni = __float2int_rn(__uint_as_float(vi[k]) * 262144.0f);
-              }
-              v[k] = make_int2(nr + rc.x - sp[k], -ni + rc.y + sq[k]);
+          const int jc = kChunk * ch + 2 * q4;  // this thread's first column in the tile
+          const int4 s0 = *reinterpret_cast<const int4*>(cs + jc);  // (8P, 8Q) of columns jc, jc + 1
+          const int4 s1 = *reinterpret_cast<const int4*>(cs + jc + 8);
+          const int sp[4] = {s0.x, s0.z, s1.x, s1.z}, sq[4] = {s0.y, s0.w, s1.y, s1.w};
+#pragma unroll 1
+          for (int hh = 0; hh < 2; ++hh) {  // rows 0-15, then 16-31 of the warp
+            uint32_t im[8];  // stashed: [4j + 2h + e]: column 8j + 2q + e of row 16 hh + rg + 8h
+            if (stashed) {
+              tmem_ld_16x256b_x2(taddr + (static_cast<uint32_t>(16 * hh) << 16) + kStashCol + kChunk * ch, im);
+              tmem_ld_wait();
             }
-            int2* dst = out_c + (int64_t)i * (i + 1) / 2 + S * kBlk + jl0;
-            const int nv = last - jl0 + 1 < 4 ? last - jl0 + 1 : 4;
-            if (nv == 4 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
-              int4* d4 = reinterpret_cast<int4*>(dst);
-              int4 w0 = make_int4(v[0].x, v[0].y, v[1].x, v[1].y), w1 = make_int4(v[2].x, v[2].y, v[3].x, v[3].y);
-              if (p.accumulate) {
-                const int4 o0 = d4[0], o1 = d4[1];
-                w0 = make_int4(w0.x + o0.x, w0.y + o0.y, w0.z + o0.z, w0.w + o0.w);
-                w1 = make_int4(w1.x + o1.x, w1.y + o1.y, w1.z + o1.z, w1.w + o1.w);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int m = 2 * hh + h;
+              const int2 rc = make_int2(__shfl_sync(0xFFFFFFFFu, rc_own.x, rg + 8 * m),
+                                        __shfl_sync(0xFFFFFFFFu, rc_own.y, rg + 8 * m));
+              const int rr = warp * 32 + rg + 8 * m, i = R * kBlk + rr;
+              const int last = R == S ? rr : kBlk - 1;  // last column of the row in the tile
+              if (i >= n_inputs || jc > last) continue;
+              const int piece = ((kChunk * ch) >> 2) + q4;
+              const uint4 re4 = *reinterpret_cast<const uint4*>(staging + rr * kBlk + ((piece ^ staging_swizzle(rr)) << 2));
+              uint32_t vi[4];
+              if (stashed) {
+                vi[0] = im[2 * h], vi[1] = im[2 * h + 1], vi[2] = im[4 + 2 * h], vi[3] = im[5 + 2 * h];
+              } else {
+                const uint4 im4 = *reinterpret_cast<const uint4*>(
+                    im_hi + rr * G::kImHiCols + (((piece - 4 * STASH) ^ staging_swizzle(rr)) << 2));
+                vi[0] = im4.x, vi[1] = im4.y, vi[2] = im4.z, vi[3] = im4.w;
               }
-              d4[0] = w0;
-              d4[1] = w1;
-            } else {
+              const uint32_t vr[4] = {re4.x, re4.y, re4.z, re4.w};
+              int2 v[4];  // columns jc, jc + 1, jc + 8, jc + 9
 #pragma unroll
               for (int k = 0; k < 4; ++k) {
-                if (k < nv) {
-                  int2 w = v[k];
+                int nr, ni;
+                if (magic) {
+                  nr = __float_as_int(fmaf(__uint_as_float(vr[k]), 262144.0f, kMagic));
+                  ni = __float_as_int(fmaf(__uint_as_float(vi[k]), 262144.0f, kMagic));
+                } else {
+                  nr = __float2int_rn(__uint_as_float(vr[k]) * 262144.0f);
+                  ni = __float2int_rn(__uint_as_float(vi[k]) * 262144.0f);
+                }
+                v[k] = make_int2(nr + rc.x - sp[k], -ni + rc.y + sq[k]);
+              }
+              int2* row_out = out_c + (int64_t)i * (i + 1) / 2 + S * kBlk;
+#pragma unroll
+              for (int jj = 0; jj < 2; ++jj) {
+                const int j0 = jc + 8 * jj;
+                if (j0 > last) continue;
+                int2* dst = row_out + j0;
+                const int nv = j0 + 1 <= last ? 2 : 1;
+                if (nv == 2 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+                  int4 w = make_int4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
                   if (p.accumulate) {
-                    const int2 o = dst[k];
-                    w.x += o.x;
-                    w.y += o.y;
+                    const int4 o = *reinterpret_cast<const int4*>(dst);
+                    w = make_int4(w.x + o.x, w.y + o.y, w.z + o.z, w.w + o.w);
                   }
-                  dst[k] = w;
+                  *reinterpret_cast<int4*>(dst) = w;
+                } else {
+#pragma unroll
+                  for (int e = 0; e < 2; ++e) {
+                    if (e < nv) {
+                      int2 w = v[2 * jj + e];
+                      if (p.accumulate) {
+                        const int2 o = dst[e];
+                        w.x += o.x;
+                        w.y += o.y;
+                      }
+                      dst[e] = w;
+                    }
+                  }
                 }
               }
             }
           }
-          __syncwarp();
         }
       }
       // the input sums are free, in this CTA and (for the column sums it receives) in the other
@@ -803,8 +812,8 @@ cudaError_t launch_pair(const CUtensorMap& map_a, const CUtensorMap& map_b, cons
 }  // namespace
 
 // The pair shapes: 96 samples with 2 raw + 3 decoded stages (Im of half the tile kept in tensor
-// memory), 128 with 2 + 2 (all of Im in tensor memory), 96 with 2 + 4 (half).
-int fused_pair_stage_samples(int variant) { return variant == 1 ? 128 : 96; }
+// memory), 128 with 2 + 2 (all of Im in tensor memory), 128 with 2 + 3 (half).
+int fused_pair_stage_samples(int variant) { return variant == 0 ? 96 : 128; }
 
 cudaError_t launch_xcorr_tc_fused_pair_ci4(const uint8_t* in, int row_chans, int variant, int n_time, int n_chan,
                                            int n_inputs, int2* out, bool accumulate, int* status, int num_sms,
@@ -840,7 +849,7 @@ cudaError_t launch_xcorr_tc_fused_pair_ci4(const uint8_t* in, int row_chans, int
     switch (variant) {
       case 0: e = launch_pair<96, 2, 3, 4>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
       case 1: e = launch_pair<128, 2, 2, 8>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
-      default: e = launch_pair<96, 2, 4, 4>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
+      default: e = launch_pair<128, 2, 3, 4>(map_a, map_b, p, static_cast<int>(items), num_sms, stream); break;
     }
     if (e != cudaSuccess) return e;
   }
