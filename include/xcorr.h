@@ -198,6 +198,23 @@ xcorr_status xcorr_dump(xcorr_plan plan, void *out, int out_on_device, unsigned 
                         void *stream, int64_t *n_samples);
 
 /*
+ * Resume an integration (checkpoint / restart; Sec. 2.4: the dumps are the
+ * correlator's durable product).  src holds a dump taken without
+ * XCORR_DUMP_RESET in the layout xcorr_dump writes -- int32 [C][P][2] for
+ * CI4 / CI8, float [C][P][2] for CF32, C * P * 8 bytes, host memory or
+ * (src_on_device != 0) device memory -- and n_samples, the samples it
+ * integrates (the count that dump reported).  The plan takes it as its
+ * running sums: later executes add to it, later dumps include it, and the
+ * integration's sample count continues from n_samples.  The copy is
+ * stream-ordered; src may be reused once the stream has passed it.  The plan
+ * must hold no integration (new, or dumped with XCORR_DUMP_RESET).
+ * Errors: INVALID_ARG (NULL src, n_samples < 0, the plan holds an
+ * integration), OVERFLOW (n_samples > max_integration), DEVICE, CUDA.
+ */
+xcorr_status xcorr_accum_load(xcorr_plan plan, const void *src, int src_on_device, int64_t n_samples,
+                              void *stream);
+
+/*
  * xcorr_execute followed by xcorr_dump with the same flags, in one call.
  * When this execute is the whole integration (the plan was reset, flags
  * hold XCORR_DUMP_RESET and not ADD_WIDE, and out is device memory) the X
@@ -551,6 +568,9 @@ typedef struct xcorr_stream_s *xcorr_stream;
 
 typedef struct {
     int64_t index;         /* dump number: block / blocks_per_dump                          */
+    int64_t first_seq;     /* sequence number of channel group 0 of the dump's first
+                              sample (Sec. 2.3: time stamps follow from the sequence numbers):
+                              index * blocks_per_dump * block_samples / N_t * n_groups      */
     int64_t n_samples;     /* samples integrated (blocks correlated x block_samples)        */
     int64_t lost_packets;  /* zero-filled packets in this dump's blocks                     */
     double latency_ms;     /* host time from closing the dump's last block to its copy

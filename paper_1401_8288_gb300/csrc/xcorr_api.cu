@@ -441,6 +441,26 @@ xcorr_status xcorr_dump(xcorr_plan plan, void* out, int out_on_device, unsigned 
   return XCORR_OK;
 }
 
+xcorr_status xcorr_accum_load(xcorr_plan plan, const void* src, int src_on_device, int64_t n_samples, void* stream) {
+  xcorr_status st = plan_ok(plan);
+  if (st != XCORR_OK) return st;
+  if (!src) return fail(XCORR_ERR_INVALID_ARG, "src is NULL");
+  if (n_samples < 0) return fail(XCORR_ERR_INVALID_ARG, "n_samples must be >= 0");
+  if (n_samples > plan->max_integration)
+    return fail(XCORR_ERR_OVERFLOW, "n_samples exceeds " + std::to_string(plan->max_integration) +
+                                        " samples (the exact range of one dump)");
+  if (!plan->fresh || plan->samples != 0)
+    return fail(XCORR_ERR_INVALID_ARG, "the plan holds an integration: dump it with XCORR_DUMP_RESET first");
+  const size_t bytes = (size_t)plan->cfg.n_channels * plan->n_pairs * 8;
+  const cudaError_t e = cudaMemcpyAsync(plan->acc, src, bytes,
+                                        src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                        static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "accumulator load");
+  plan->samples = n_samples;
+  plan->fresh = false;
+  return XCORR_OK;
+}
+
 xcorr_status xcorr_execute_dump(xcorr_plan plan, const void* d_in, int n_time, void* out, int out_on_device,
                                 unsigned flags, void* stream, int64_t* n_samples) {
   xcorr_status st = check_execute(plan, d_in, n_time);

@@ -481,6 +481,7 @@ xcorr_status xcorr_stream_wait_dump(xcorr_stream s, int64_t k, int timeout_ms, x
   if (!s->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms), [&] { return r->done; }))
     return xc::set_error(XCORR_ERR_CUDA, "timed out waiting for the dump copy");
   rec->index = r->index;
+  rec->first_seq = r->index * s->cfg.blocks_per_dump * (s->cfg.block_samples / s->dg.nt) * s->dg.n_groups;
   rec->n_samples = r->n_samples;
   rec->lost_packets = r->lost;
   rec->latency_ms = r->latency_ms;

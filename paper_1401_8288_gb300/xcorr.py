@@ -40,7 +40,7 @@ EXPORTS = ("xcorr_plan_create", "xcorr_execute", "xcorr_dump", "xcorr_sync", "xc
            "xcorr_execute_dump_host", "xcorr_bdi_create", "xcorr_bdi_step", "xcorr_bdi_destroy",
            "xcorr_watchdog_selftest", "xcorr_autotune_cached", "xcorr_tuning_cache_load",
            "xcorr_tuning_cache_save", "xcorr_tuning_cache_clear", "xcorr_batch_set_subarray_variants",
-           "xcorr_batch_get_subarray_variants", "xcorr_batch_autotune")
+           "xcorr_batch_get_subarray_variants", "xcorr_batch_autotune", "xcorr_accum_load")
 XCORR_PACKET_HEADER_BYTES = 16
 XCORR_EVENT_OPEN, XCORR_EVENT_CLOSE = 1, 2
 PEAK_KINDS = {"tc_e4m3": 0, "tc_bf16": 1, "mma_sync_s8": 2, "dp4a": 3}
@@ -92,7 +92,7 @@ class xcorr_block_event(ctypes.Structure):
 
 
 class xcorr_dump_record(ctypes.Structure):
-    _fields_ = [("index", ctypes.c_int64), ("n_samples", ctypes.c_int64),
+    _fields_ = [("index", ctypes.c_int64), ("first_seq", ctypes.c_int64), ("n_samples", ctypes.c_int64),
                 ("lost_packets", ctypes.c_int64), ("latency_ms", ctypes.c_double),
                 ("data", ctypes.c_void_p)]
 
@@ -120,6 +120,7 @@ def load():
                 "xcorr_execute": [vp, vp, i, vp],
                 "xcorr_dump": [vp, vp, i, u, vp, ctypes.POINTER(i64)],
                 "xcorr_execute_dump": [vp, vp, i, vp, i, u, vp, ctypes.POINTER(i64)],
+                "xcorr_accum_load": [vp, vp, i, i64, vp],
                 "xcorr_sync": [vp, vp],
                 "xcorr_plan_query": [vp, ctypes.POINTER(xcorr_plan_info)],
                 "xcorr_destroy": [vp],
@@ -209,6 +210,10 @@ def xcorr_dump(plan, out: int, out_on_device: bool, flags: int = 0, stream: int 
     n = ctypes.c_int64()
     _check(load().xcorr_dump(plan, out, int(out_on_device), flags, stream, ctypes.byref(n)))
     return n.value
+
+
+def xcorr_accum_load(plan, src: int, src_on_device: bool, n_samples: int, stream: int = 0) -> None:
+    _check(load().xcorr_accum_load(plan, src, int(src_on_device), n_samples, stream))
 
 
 def xcorr_execute_dump(plan, d_in: int, n_time: int, out: int, out_on_device: bool,
@@ -523,8 +528,8 @@ class Stream:
         import numpy as np
         r = xcorr_dump_record()
         _check(load().xcorr_stream_wait_dump(self.handle, k, timeout_ms, ctypes.byref(r)))
-        out = {"index": r.index, "n_samples": r.n_samples, "lost_packets": r.lost_packets,
-               "latency_ms": r.latency_ms, "data": None}
+        out = {"index": r.index, "first_seq": r.first_seq, "n_samples": r.n_samples,
+               "lost_packets": r.lost_packets, "latency_ms": r.latency_ms, "data": None}
         if r.data and copy:
             n = int(np.prod(self.out_shape))
             buf = (ctypes.c_int32 * n).from_address(r.data)
@@ -703,6 +708,15 @@ class Plan:
         self.samples = xcorr_dump(self.handle, out.data_ptr(), out.is_cuda, flags,
                                   self._stream(stream))
         return out
+
+    def accum_load(self, src, n_samples: int, stream=None):
+        """Resume an integration from a dump taken with reset=False: src is that dump (a host or
+        CUDA tensor in the plan's output layout) and n_samples the samples it integrates."""
+        if (not src.is_contiguous() or src.numel() != self.n_channels * self.info["n_pairs"] * 2
+                or src.dtype != self._out_dtype(False)):
+            raise ValueError("src must be a contiguous [C][P][2] dump of this plan, in its dtype")
+        xcorr_accum_load(self.handle, src.data_ptr(), src.is_cuda, n_samples, self._stream(stream))
+        self.samples = n_samples
 
     def execute_dump(self, x, out=None, reset: bool = True, wide: bool = False, stream=None):
         """execute(x) then dump(...), fused into one pass when x is the whole integration."""

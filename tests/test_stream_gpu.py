@@ -78,6 +78,8 @@ def test_in_order_stream_matches_oracle(torch, engine, tuning):
     assert len(dumps) == 3
     for k, d in enumerate(dumps):
         assert d["index"] == k and d["n_samples"] == 2 * BLOCK and d["lost_packets"] == 0
+        # the sequence number of the dump's first sample: its packets' time block x channel groups
+        assert d["first_seq"] == (k * 2 * BLOCK // NT) * (N_CHAN // NCH)
         assert np.array_equal(d["data"].astype(np.int64), want[k])
     assert counters["placed"] == n_blocks * P and counters["lost"] == 0
 

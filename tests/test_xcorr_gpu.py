@@ -133,6 +133,45 @@ def test_dump_reset_and_wide_fold(torch, engine):
         assert n == 96 and np.array_equal(host, want)
 
 
+@pytest.mark.parametrize("fmt,engine", [("ci4", "tensor"), ("ci4", "cuda_core"), ("ci8", "tensor"),
+                                        ("ci8", "cuda_core"), ("cf32", "tensor")])
+def test_resume_an_integration_from_a_dump(torch, fmt, engine):
+    # checkpoint / restart: a dump taken without reset (to host memory), loaded into a new plan,
+    # continues the integration; the result is the uninterrupted one, bit for bit
+    x = {"ci4": lambda: synth.uniform_ci4(300, 3, 40, seed=91, lo=-8, hi=7),
+         "ci8": lambda: synth.uniform_ci8(300, 3, 40, seed=92),
+         "cf32": lambda: synth.gaussian_cf32(300, 3, 40, seed=93)}[fmt]()
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    with xcorr.Plan(40, 3, 200, fmt=fmt, engine=engine) as a:
+        a.execute(xd[:120])
+        ck = torch.zeros((3, a.info["n_pairs"], 2), dtype=a._out_dtype(False)).pin_memory()
+        a.dump(out=ck, reset=False)
+        a.execute(xd[120:])
+        whole = a.dump(reset=True)
+        a.sync()
+        n_ck = 120
+        # the plan holds nothing after the reset dump: a load is accepted, a second one is not
+        a.accum_load(ck, n_ck)
+        with pytest.raises(xcorr.XcorrError):
+            a.accum_load(ck, n_ck)
+    with xcorr.Plan(40, 3, 200, fmt=fmt, engine=engine) as b:
+        with pytest.raises(xcorr.XcorrError):
+            b.accum_load(ck, -1)
+        with pytest.raises(xcorr.XcorrError):
+            b.accum_load(ck, b.info["max_integration"] + 1)
+        b.accum_load(ck, n_ck)
+        b.execute(xd[120:])
+        got = b.dump(reset=True)
+        b.sync()
+        assert b.samples == 300
+    assert np.array_equal(got.cpu().numpy(), whole.cpu().numpy())
+    if fmt == "cf32":
+        e, _ = normalised_error(got.cpu().numpy(), oracle.correlate(oracle.FMT_CF32, x), 80)
+        assert e.max() <= 1e-6, e.max()
+    else:
+        assert np.array_equal(got.cpu().numpy(), oracle.correlate(oracle.FMT_CI4 if fmt == "ci4" else oracle.FMT_CI8, x))
+
+
 @pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("fmt", ["ci4", "ci8"])
 def test_input_at_any_byte_offset(torch, engine, fmt):
