@@ -299,11 +299,13 @@ xcorr_status xcorr_autotune_cached(xcorr_plan plan, const void *d_in, int n_time
 /*
  * The process's tuning cache, in files.  save writes every entry, one JSON
  * object per line with the fields scope ("plan" or "batch"), device, sms, fmt,
- * n_inputs, n_channels, n_time, stage_variant, groups, x_streams, unfused and
- * us (the recorded time, microseconds); the file is replaced whole (written
- * to path.tmp, then renamed).  load merges a file's entries into the cache
- * (an entry for the same problem is replaced); a line without every field,
- * or with a value out of range, is skipped and counted in *n_skipped.  clear
+ * n_inputs, n_channels, n_time, stage_variant, groups, x_streams, unfused,
+ * us (the recorded time, microseconds) and shape_table (the revision of this
+ * library's table of launch shapes, which gives stage_variant its meaning);
+ * the file is replaced whole (written to path.tmp, then renamed).  load
+ * merges a file's entries into the cache (an entry for the same problem is
+ * replaced); a line without every field, with a value out of range, or from
+ * another shape-table revision is skipped and counted in *n_skipped.  clear
  * empties the cache.  n_loaded, n_skipped and n_saved may be NULL.
  * Errors: INVALID_ARG (NULL path, a file that cannot be opened or written).
  */

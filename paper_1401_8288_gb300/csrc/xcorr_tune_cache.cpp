@@ -7,7 +7,9 @@
 // file format is one JSON object per line with exactly the fields save()
 // writes; load() reads those fields back and skips (and counts) any line it
 // cannot read, so a file edited by hand or written by another version does not
-// stop a run.
+// stop a run.  Shapes are stored by number, so each line also carries the
+// revision of the library's shape table (kShapeTable): a line from another
+// revision names other shapes and is skipped.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -20,6 +22,10 @@
 
 namespace xc {
 namespace {
+
+// Revision of the launch-shape table the stored stage_variant numbers refer to; raised whenever
+// a shape number comes to mean another launch.
+constexpr int kShapeTable = 2;
 
 using Key = std::tuple<std::string, std::string, int, int, int, int, int>;  // scope, device, sms, fmt, N_i, C, T
 struct Entry {
@@ -131,6 +137,8 @@ xcorr_status xcorr_tuning_cache_load(const char* path, int* n_loaded, int* n_ski
               xc::int_field(line, "n_time", &k.n_time) && xc::int_field(line, "stage_variant", &t.stage_variant) &&
               xc::int_field(line, "groups", &t.groups) && xc::int_field(line, "x_streams", &t.x_streams) &&
               xc::int_field(line, "unfused", &t.unfused) && xc::int_field(line, "us", &ms_milli);
+    int table = -1;
+    ok = ok && xc::int_field(line, "shape_table", &table) && table == xc::kShapeTable;
     ok = ok && t.stage_variant >= 0 && t.stage_variant < xc::kFusedVariants && t.groups >= 0 &&
          t.groups <= xc::kMaxGroups && (t.x_streams == 1 || t.x_streams == 2) && (t.unfused == 0 || t.unfused == 1);
     if (!ok) {
@@ -160,10 +168,10 @@ xcorr_status xcorr_tuning_cache_save(const char* path, int* n_saved) {
       std::fprintf(f,
                    "{\"scope\": \"%s\", \"device\": \"%s\", \"sms\": %d, \"fmt\": %d, \"n_inputs\": %d, "
                    "\"n_channels\": %d, \"n_time\": %d, \"stage_variant\": %d, \"groups\": %d, \"x_streams\": %d, "
-                   "\"unfused\": %d, \"us\": %d}\n",
+                   "\"unfused\": %d, \"us\": %d, \"shape_table\": %d}\n",
                    std::get<0>(k).c_str(), std::get<1>(k).c_str(), std::get<2>(k), std::get<3>(k), std::get<4>(k),
                    std::get<5>(k), std::get<6>(k), e.t.stage_variant, e.t.groups, e.t.x_streams, e.t.unfused,
-                   static_cast<int>(e.ms * 1000.f + 0.5f));
+                   static_cast<int>(e.ms * 1000.f + 0.5f), xc::kShapeTable);
       ++n;
     }
   }

@@ -103,14 +103,15 @@ def test_tuning_cache_file_round_trip(lib, tmp_path):
     import json
     good = {"scope": "plan", "device": "NVIDIA GB300", "sms": 152, "fmt": 0, "n_inputs": 512,
             "n_channels": 512, "n_time": 2048, "stage_variant": 4, "groups": 1, "x_streams": 1,
-            "unfused": 0, "us": 501}
+            "unfused": 0, "us": 501, "shape_table": 2}
     batch = dict(good, scope="batch", n_inputs=64, n_channels=64, n_time=1024, stage_variant=3, us=12)
     path = tmp_path / "tuning.jsonl"
     lines = [json.dumps(good), "not json at all", json.dumps(dict(good, stage_variant=99)),
-             json.dumps({k: v for k, v in good.items() if k != "groups"}), json.dumps(batch), ""]
+             json.dumps({k: v for k, v in good.items() if k != "groups"}), json.dumps(batch),
+             json.dumps(dict(good, shape_table=1)), ""]  # a line of another shape-table revision
     path.write_text("\n".join(lines) + "\n")
     xcorr.xcorr_tuning_cache_clear()
-    assert xcorr.xcorr_tuning_cache_load(str(path)) == (2, 3)
+    assert xcorr.xcorr_tuning_cache_load(str(path)) == (2, 4)
     out = tmp_path / "saved.jsonl"
     assert xcorr.xcorr_tuning_cache_save(str(out)) == 2
     saved = [json.loads(line) for line in out.read_text().splitlines()]
