@@ -99,8 +99,16 @@ struct PGeom {
   static constexpr int kAcols = KT / 2;      // one A stage: KT / 4 columns of real codes, then imaginary
   static constexpr int kRowsB = KT / (kGroupWarps * 32 / 4);  // B rows per decoder thread and stage
   static constexpr int kSteps = KT / 32;                 // MMA steps (32 samples) per stage
-  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kBStage + kStagingBytes + kImHiBytes + kSumsBytes +
-                               kScratchBytes + kRscratchBytes + kBarrierBytes;
+  // byte offsets of the buffers from the 1024-aligned start of shared memory; the kernel takes
+  // its pointers from these, and the allocation is their end (plus the alignment slack)
+  static constexpr int kOffBpl = RAW * kRawStage;
+  static constexpr int kOffStaging = kOffBpl + DEC * kBStage;
+  static constexpr int kOffImHi = kOffStaging + kStagingBytes;
+  static constexpr int kOffSums = kOffImHi + kImHiBytes;
+  static constexpr int kOffScratch = kOffSums + kSumsBytes;
+  static constexpr int kOffRscratch = kOffScratch + kScratchBytes;
+  static constexpr int kOffBarriers = kOffRscratch + kRscratchBytes;
+  static constexpr int kSmem = 1024 + kOffBarriers + kBarrierBytes;
   static_assert(KT % 32 == 0, "stages hold whole MMA steps and whole 32-row B passes");
   // each decoder group waits only on its own raw slots (stage s uses slot s % RAW, decoded by group
   // s % 2), so no group can test a raw barrier a phase ahead of another group's fill
@@ -166,13 +174,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* raw = smem;                      // [stage][row tile | half column tile]
-  uint8_t* bpl = raw + RAW * G::kRawStage;  // [stage][real plane | imaginary plane]
-  uint32_t* staging = reinterpret_cast<uint32_t*>(bpl + DEC * G::kBStage);  // Re [row][16-byte chunk ^ swz(row)]
-  uint32_t* im_hi = staging + kBlk * kBlk;                 // Im past the stash, [row][16-byte chunk ^ swz(row)]
-  int2* sums = reinterpret_cast<int2*>(im_hi + G::kImHiBytes / 4);
-  int2* scratch = sums + 2 * 2 * kBlk;
-  int2* rscratch = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(scratch) + kScratchBytes);
-  uint64_t* raw_full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(rscratch) + kRscratchBytes);
+  uint8_t* bpl = smem + G::kOffBpl;  // [stage][real plane | imaginary plane | negated real plane]
+  uint32_t* staging = reinterpret_cast<uint32_t*>(smem + G::kOffStaging);  // Re [row][16-byte chunk ^ swz(row)]
+  uint32_t* im_hi = reinterpret_cast<uint32_t*>(smem + G::kOffImHi);  // Im past the stash, same layout
+  int2* sums = reinterpret_cast<int2*>(smem + G::kOffSums);
+  int2* scratch = reinterpret_cast<int2*>(smem + G::kOffScratch);
+  int2* rscratch = reinterpret_cast<int2*>(smem + G::kOffRscratch);
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem + G::kOffBarriers);
   uint64_t* raw_empty = raw_full + RAW;
   uint64_t* dec_full = raw_empty + RAW;  // even CTA: both CTAs' decoders filled the stage
   uint64_t* dec_empty = dec_full + DEC;  // both CTAs: the pair's MMAs are done with the stage

@@ -82,8 +82,15 @@ struct TGeom {
   static constexpr int kAcols = KT / 2;        // one A stage: KT / 4 columns of real codes, then imaginary
   static constexpr int kRowsB = KT / (kDecThreads / 8);  // B rows per decoder thread and stage
   static constexpr int kSteps = KT / 32;                 // MMA steps (32 samples) per stage
-  static constexpr int kSmem = 1024 + RAW * kRawStage + DEC * kBStage + kStagingBytes + kRowcBytes +
-                               kSumsBytes + kScratchBytes + kBarrierBytes;
+  // byte offsets of the buffers from the 1024-aligned start of shared memory; the kernel takes
+  // its pointers from these, and the allocation is their end (plus the alignment slack)
+  static constexpr int kOffBpl = RAW * kRawStage;
+  static constexpr int kOffStaging = kOffBpl + DEC * kBStage;
+  static constexpr int kOffRowc = kOffStaging + kStagingBytes;
+  static constexpr int kOffSums = kOffRowc + kRowcBytes;
+  static constexpr int kOffScratch = kOffSums + kSumsBytes;
+  static constexpr int kOffBarriers = kOffScratch + kScratchBytes;
+  static constexpr int kSmem = 1024 + kOffBarriers + kBarrierBytes;
   static_assert(KT % 32 == 0, "stages hold whole MMA steps and whole 32-row B passes");
   static_assert(DEC * kAcols <= static_cast<int>(kTmemCols - kAcol0), "A stages fit beside the accumulator");
   static_assert((2 * RAW + 2 * DEC + 7) * 8 + 8 <= kBarrierBytes, "barrier area");
@@ -196,12 +203,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* raw = smem;
-  uint8_t* bpl = raw + RAW * G::kRawStage;
-  uint32_t* staging = reinterpret_cast<uint32_t*>(bpl + DEC * G::kBStage);  // Re [row][16-byte chunk ^ swz(row)]
-  int2* rowc = reinterpret_cast<int2*>(staging + kBlk * kBlk);                // [row]
-  int2* sums = rowc + kBlk;
-  int2* scratch = sums + 2 * 2 * kBlk;
-  uint64_t* raw_full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(scratch) + kScratchBytes);
+  uint8_t* bpl = smem + G::kOffBpl;
+  uint32_t* staging = reinterpret_cast<uint32_t*>(smem + G::kOffStaging);  // Re [row][16-byte chunk ^ swz(row)]
+  int2* rowc = reinterpret_cast<int2*>(smem + G::kOffRowc);                 // [row]
+  int2* sums = reinterpret_cast<int2*>(smem + G::kOffSums);
+  int2* scratch = reinterpret_cast<int2*>(smem + G::kOffScratch);
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem + G::kOffBarriers);
   uint64_t* raw_empty = raw_full + RAW;
   uint64_t* dec_full = raw_empty + RAW;
   uint64_t* dec_empty = dec_full + DEC;
