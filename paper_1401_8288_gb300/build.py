@@ -91,7 +91,8 @@ def _build(verbose: bool, extra_flags: list[str] | None) -> str:
             list(ex.map(run, jobs))
     if _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
+        # -ldl: the NVTX ranges look up a profiler's injection library with dlopen
+        run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

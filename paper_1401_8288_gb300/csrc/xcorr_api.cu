@@ -6,6 +6,7 @@
 #include <string>
 
 #include "xcorr_internal.h"
+#include "xcorr_nvtx.h"
 
 namespace {
 
@@ -393,6 +394,7 @@ xcorr_status xcorr_plan_create(xcorr_plan* out, const xcorr_config* cfg) {
 }
 
 xcorr_status xcorr_execute(xcorr_plan plan, const void* d_in, int n_time, void* stream) {
+  xc::NvtxRange range("xcorr_execute");
   xcorr_status st = check_execute(plan, d_in, n_time);
   if (st != XCORR_OK) return st;
   st = run_execute(plan, d_in, n_time, plan->acc, plan->fresh, static_cast<cudaStream_t>(stream));
@@ -404,6 +406,7 @@ xcorr_status xcorr_execute(xcorr_plan plan, const void* d_in, int n_time, void* 
 
 xcorr_status xcorr_dump(xcorr_plan plan, void* out, int out_on_device, unsigned flags, void* stream,
                         int64_t* n_samples) {
+  xc::NvtxRange range("xcorr_dump");
   xcorr_status st = plan_ok(plan);
   if (st != XCORR_OK) return st;
   if (!out) return fail(XCORR_ERR_INVALID_ARG, "out is NULL");
@@ -463,6 +466,7 @@ xcorr_status xcorr_accum_load(xcorr_plan plan, const void* src, int src_on_devic
 
 xcorr_status xcorr_execute_dump(xcorr_plan plan, const void* d_in, int n_time, void* out, int out_on_device,
                                 unsigned flags, void* stream, int64_t* n_samples) {
+  xc::NvtxRange range("xcorr_execute_dump");
   xcorr_status st = check_execute(plan, d_in, n_time);
   if (st != XCORR_OK) return st;
   if (!out) return fail(XCORR_ERR_INVALID_ARG, "out is NULL");
@@ -486,6 +490,7 @@ xcorr_status xcorr_execute_dump(xcorr_plan plan, const void* d_in, int n_time, v
 
 xcorr_status xcorr_execute_dump_host(xcorr_plan plan, const void* h_in, int n_time, void* h_out, int n_groups,
                                      void* stream) {
+  xc::NvtxRange range("xcorr_execute_dump_host");
   xcorr_status st = check_execute(plan, h_in, n_time);
   if (st != XCORR_OK) return st;
   if (!h_out) return fail(XCORR_ERR_INVALID_ARG, "h_out is NULL");

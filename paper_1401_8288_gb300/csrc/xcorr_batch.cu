@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "xcorr_internal.h"
+#include "xcorr_nvtx.h"
 
 constexpr int kBatchClasses = 3;  // the tensor-memory-A kernel's batch shapes (plan shapes 4-6)
 constexpr int kSoloStreams = 4;   // streams the subarrays with a shape of their own are dealt over
@@ -477,6 +478,7 @@ xcorr_status xcorr_batch_autotune(xcorr_batch b, const void* const* d_ins, void*
 }
 
 xcorr_status xcorr_batch_execute(xcorr_batch b, const void* const* d_ins, void* const* d_outs, void* stream) {
+  xc::NvtxRange range("xcorr_batch_execute");
   if (!b || !d_ins || !d_outs) return bfail(XCORR_ERR_INVALID_ARG, "batch, d_ins and d_outs must not be NULL");
   for (int s = 0; s < b->n; ++s)
     if (!d_ins[s] || !d_outs[s]) return bfail(XCORR_ERR_INVALID_ARG, "a subarray buffer is NULL");
@@ -531,6 +533,7 @@ xcorr_status xcorr_batch_capture(xcorr_batch b, const void* const* d_ins, void* 
 }
 
 xcorr_status xcorr_batch_replay(xcorr_batch b, void* stream) {
+  xc::NvtxRange range("xcorr_batch_replay");
   if (!b || !b->graph_exec) return bfail(XCORR_ERR_INVALID_ARG, "no captured graph: call xcorr_batch_capture first");
   cudaError_t e = cudaGraphLaunch(b->graph_exec, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return bfail(XCORR_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));

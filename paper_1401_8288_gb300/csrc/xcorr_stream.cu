@@ -23,6 +23,7 @@
 
 #include "xcorr_internal.h"
 #include "xcorr_stream.h"
+#include "xcorr_nvtx.h"
 
 namespace xc {
 namespace {
@@ -398,6 +399,7 @@ xcorr_status xcorr_stream_acquire(xcorr_stream s, void** chunk, int64_t* capacit
 }
 
 xcorr_status xcorr_stream_commit(xcorr_stream s, int64_t n_packets) {
+  xc::NvtxRange range("xcorr_stream_commit");
   xcorr_status st = stream_ok(s);
   if (st != XCORR_OK) return st;
   if (s->acquired < 0) return xc::set_error(XCORR_ERR_INVALID_ARG, "no chunk acquired");
