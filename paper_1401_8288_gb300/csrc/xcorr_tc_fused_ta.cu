@@ -322,21 +322,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         // registers, stored to TMEM eight columns at a time
         const uint32_t ta = tmem + a_lanes + kAcol0 + static_cast<uint32_t>(d * G::kAcols);
         static_assert(KT % 32 == 0, "whole pairs of 16-sample blocks");
+        // four blocks per pair of stores (sixteen columns), then a pair of blocks if KT / 16 is
+        // not a multiple of four
 #pragma unroll
-        for (int sb = 0; sb < KT / 16; sb += 2) {
-          uint32_t x0, x1, x2, x3, re0, im0, re1, im1, re2, im2, re3, im3;
-          ldmatrix_t_b8_x2(smem_u32(raw_a + (16 * sb + lane) * 128 + apos), x0, x1, x2, x3);
-          offset_codes(x0, re0, im0);
-          offset_codes(x1, re1, im1);
-          offset_codes(x2, re2, im2);
-          offset_codes(x3, re3, im3);
-          // the two blocks' codes of one input add per byte (<= 30) before the dp4a
-          sar0 = __dp4a(re0 + re2, 0x01010101u, sar0);
-          sai0 = __dp4a(im0 + im2, 0x01010101u, sai0);
-          sar1 = __dp4a(re1 + re3, 0x01010101u, sar1);
-          sai1 = __dp4a(im1 + im3, 0x01010101u, sai1);
-          tmem_st_16x128b_x2(ta + 4 * sb, re0, re1, re2, re3);
-          tmem_st_16x128b_x2(ta + KT / 4 + 4 * sb, im0, im1, im2, im3);
+        for (int sb = 0; sb < KT / 16; sb += 4) {
+          const int nb = KT / 16 - sb >= 4 ? 2 : 1;  // ldmatrix pairs of blocks in this group
+          uint32_t re[8], im[8];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h >= nb) break;
+            uint32_t x0, x1, x2, x3;
+            ldmatrix_t_b8_x2(smem_u32(raw_a + (16 * (sb + 2 * h) + lane) * 128 + apos), x0, x1, x2, x3);
+            offset_codes(x0, re[4 * h], im[4 * h]);
+            offset_codes(x1, re[4 * h + 1], im[4 * h + 1]);
+            offset_codes(x2, re[4 * h + 2], im[4 * h + 2]);
+            offset_codes(x3, re[4 * h + 3], im[4 * h + 3]);
+            // the two blocks' codes of one input add per byte (<= 30) before the dp4a
+            sar0 = __dp4a(re[4 * h] + re[4 * h + 2], 0x01010101u, sar0);
+            sai0 = __dp4a(im[4 * h] + im[4 * h + 2], 0x01010101u, sai0);
+            sar1 = __dp4a(re[4 * h + 1] + re[4 * h + 3], 0x01010101u, sar1);
+            sai1 = __dp4a(im[4 * h + 1] + im[4 * h + 3], 0x01010101u, sai1);
+          }
+          if (nb == 2) {
+            tmem_st_16x128b_x4(ta + 4 * sb, re);
+            tmem_st_16x128b_x4(ta + KT / 4 + 4 * sb, im);
+          } else {
+            tmem_st_16x128b_x2(ta + 4 * sb, re[0], re[1], re[2], re[3]);
+            tmem_st_16x128b_x2(ta + KT / 4 + 4 * sb, im[0], im[1], im[2], im[3]);
+          }
         }
         // B operand: real and imaginary planes in shared memory at the raw chunk's swizzled offset
         {
