@@ -16,7 +16,7 @@ namespace fused {
 constexpr int kBlk = 128;                        // inputs per tile
 constexpr uint32_t kNibbleTop = 0x88888888u;     // t -> t + 8 on every nibble
 constexpr uint32_t kLowNibbles = 0x0F0F0F0Fu;
-constexpr int kPrefetchSamples = 512;            // L2 prefetch distance along time
+constexpr int kPrefetchSamples = 128;            // L2 prefetch distance along time (one 128-sample stage)
 
 // Tile pair p of the packed lower triangle of tiles: p = I (I + 1) / 2 + J.
 __device__ __forceinline__ void tile_pair(int p, int& I, int& J) {
